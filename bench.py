@@ -1,0 +1,385 @@
+"""Benchmark of the interval solver on one GB300 (or N, as independent replicas).
+
+A step is one complete solve of the workload (every per-box stage: FP32 prefilter, FP64
+evaluation and exclusion, Hansen-Sengupta contraction, accept / split, queue compaction
+and refill) with the system already resident on the device.  Default workload: the
+seeded n=6 sparse system (6 equations x 8 monomials, degree <= 3, integer coefficients,
+planted root, box [-4,4]^6, tol 1e-6).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload n6|n2|n10|batched]
+                  [--impl ivsolve|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1802_00330_gb300 import synth  # noqa: E402
+
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def workload(name):
+    if name == "n2":
+        return [synth.config_n2()], "n2 x^2+y^2-1, x^2-y on [-2,2]^2, tol 1e-8, HS on"
+    if name == "n6":
+        return [synth.config_n6()], ("n6 seeded sparse system: 6 eq x 8 monomials, deg<=3, int coef [-5,5], "
+                                     "planted root, box [-4,4]^6, tol 1e-6, HS on, FP32 prefilter")
+    if name == "n10":
+        return [synth.config_n10()], ("n10 seeded sparse system: 10 eq x 12 monomials, deg<=4, coef k/2^20, "
+                                      "planted root, box [-2,2]^10, tol 1e-6")
+    if name == "batched":
+        return synth.config_batched(), ("batched: 4096 seeded systems, n~U{2..8}, 4-10 monomials/eq, deg<=3, "
+                                         "int coef [-5,5], planted roots, box [-4,4]^n, tol 1e-6")
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ---- algorithmic work per box (FP64 operations the method needs) --------------------
+def eval_ops(s, polys=None):
+    """Directed FP64 operations of one natural-form evaluation of the given polynomials:
+    per factor x^k a chain of k-1 products per end, per extra factor one interval product
+    (2 directed products with the sign-selected ends), 2 for the coefficient, 2 per sum."""
+    ops = 0
+    for i in range(s.n_eqs):
+        ts = list(s.terms_of(i))
+        for q, t in enumerate(ts):
+            e = [int(v) for v in s.exps[t] if v]
+            if e:
+                ops += sum(2 * (k - 1) for k in e) + 2 * (len(e) - 1) + 2
+            if q:
+                ops += 2
+    return ops
+
+
+def jac_ops(s):
+    ops = 0
+    for i in range(s.n_eqs):
+        for j in range(s.n_vars):
+            ts = [t for t in s.terms_of(i) if s.exps[t, j] > 0]
+            for q, t in enumerate(ts):
+                e = [int(v) - (1 if jj == j else 0) for jj, v in enumerate(s.exps[t])]
+                e = [k for k in e if k]
+                if e:
+                    ops += sum(2 * (k - 1) for k in e) + 2 * (len(e) - 1) + 2
+                if q:
+                    ops += 2
+    return ops
+
+
+def hs_ops(s):
+    """One Hansen-Sengupta sweep: J(X), mid(J) (2 per entry), in-place Gauss-Jordan
+    (n^2 divisions + 2 n^2 (n-1)), f(x) (thin evaluation), M = B J (4 n^3 - 2 n^2),
+    r = B f (4 n^2 - 2 n), Gauss-Seidel ((n-1) * 6 + 4 per row), midpoints 2n."""
+    n = s.n_vars
+    return (jac_ops(s) + 2 * n * n + n * n + 2 * n * n * (n - 1) + eval_ops(s) + 4 * n ** 3 - 2 * n * n
+            + 4 * n * n - 2 * n + n * (6 * (n - 1) + 4) + 2 * n)
+
+
+# ---- clocks --------------------------------------------------------------------------
+class ClockSampler:
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = []
+        smax = 0.0
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- the oracle as CPU baseline / reference arm ---------------------------------------
+def oracle_sample(systems, budget_boxes):
+    import oracle
+    t = time.perf_counter()
+    boxes = 0
+    for s in systems:
+        r = oracle.solve(s, max_boxes=budget_boxes)
+        boxes += r["stats"]["boxes"]
+        if time.perf_counter() - t > 60:
+            break
+    dt = time.perf_counter() - t
+    return boxes, dt
+
+
+def run_reference(args, systems, desc, rank, world):
+    if rank != 0:
+        return
+    budget = args.ref_boxes
+    for _ in range(args.warmup):
+        oracle_sample(systems[:1], budget // 10)
+    tot_b, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        b, t = oracle_sample(systems[:1], budget)
+        tot_b += b
+        tot_t += t
+    v = tot_b / tot_t
+    line = {"impl": "reference", "metric": "boxes/sec", "value": v, "unit": "boxes/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc},
+            "cpu_baseline": {"value": v, "unit": "boxes/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {budget} boxes (LIFO order) of the {args.workload} solve per step"},
+            "e2e": {"value": v, "unit": "boxes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- the GPU arm --------------------------------------------------------------------
+def run_gpu(args, systems, desc, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_1802_00330_gb300 import _binding as B
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+
+    stream = torch.cuda.Stream()
+    plan = B.Plan(systems, stream=stream, wave_children=args.wave_children)       # graph path
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
+
+    def one_step():
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.run()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    for _ in range(args.warmup):
+        one_step()
+    ref = plan.result(0)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if dist:
+        td.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    step_t = []
+    boxes = 0
+    launches = 0
+    ktimes = {}
+    for _ in range(args.steps):
+        step_t.append(one_step())
+        st = plan.stats()
+        boxes += st["boxes"]
+        launches += st["launches"]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    if dist:
+        td.barrier()
+    ck = clocks.stop()
+    t_dev = float(np.sum(step_t))
+    if dist:
+        tt = torch.tensor([t_dev], device="cuda")
+        td.all_reduce(tt, op=td.ReduceOp.MAX)
+        t_dev = float(tt.item())
+        bb = torch.tensor([boxes], device="cuda", dtype=torch.float64)
+        td.all_reduce(bb)
+        boxes_all = float(bb.item())
+    else:
+        boxes_all = boxes
+    value = boxes_all / t_dev
+    sys_per_s = world * len(systems) * args.steps / t_dev
+
+    # parity guard: the timed solve's result equals the warm-up solve's
+    res = plan.result(0)
+    assert np.array_equal(res["lo"], ref["lo"]) and np.array_equal(res["hi"], ref["hi"])
+
+    # plain FP64 path (prefilter off) on the same workload, same GPU
+    plan64 = B.Plan(systems, opts={"prefilter_fp32": 0}, stream=stream, wave_children=args.wave_children)
+    for _ in range(2):
+        plan64.run()
+    t64 = []
+    b64 = 0
+    for _ in range(max(1, args.steps // 2)):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan64.run()
+        b.record(stream)
+        b.synchronize()
+        t64.append(a.elapsed_time(b) / 1e3)
+        b64 += plan64.stats()["boxes"]
+    r64 = plan64.result(0)
+    assert np.array_equal(r64["lo"], ref["lo"]) and np.array_equal(r64["hi"], ref["hi"])
+    plan64.close()
+
+    # e2e through the public host API: host system in, host boxes out
+    s0 = systems[0]
+    e2e_t = []
+    e2e_boxes = 0
+    h2d = (s0.eq_offsets.nbytes + s0.coef_lo.nbytes + s0.coef_hi.nbytes + s0.exps.nbytes
+           + s0.box_lo.nbytes + s0.box_hi.nbytes)
+    d2h = 0
+    if len(systems) == 1:
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            r = B.solve(s0)
+            e2e_t.append(time.perf_counter() - t0)
+            e2e_boxes += r["stats"]["boxes"]
+            d2h = r["lo"].nbytes + r["hi"].nbytes + r["flags"].nbytes + r["depth"].nbytes
+    else:
+        for _ in range(max(1, args.steps // 2)):
+            t0 = time.perf_counter()
+            outs = B.solve_batch(systems)
+            e2e_t.append(time.perf_counter() - t0)
+            e2e_boxes += sum(o["stats"]["boxes"] for o in outs)
+    e2e = {"value": e2e_boxes / float(np.sum(e2e_t)), "unit": "boxes/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h)}
+
+    # per-kernel device time: the same solve through the host loop with CUDA events
+    # around every stage (a graph body cannot hold event nodes), over the same K steps
+    prof = B.Plan(systems, stream=stream, profile=True, wave_children=args.wave_children)
+    prof.run()
+    ktimes = {}
+    prof_boxes = 0
+    prof_t = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prof.run()
+        prof_t.append(time.perf_counter() - t0)
+        prof_boxes += prof.stats()["boxes"]
+        for k, (nl, ms) in prof.kernel_times().items():
+            pl, pm = ktimes.get(k, (0, 0.0))
+            ktimes[k] = (pl + nl, pm + ms)
+    pst = prof.stats()
+    prof.close()
+
+    # roofline of the dominant kernel class
+    fp64_rate, _ = B.probe_rate(0, local_rank)
+    fp32_rate, _ = B.probe_rate(1, local_rank)
+    dom = max(ktimes.items(), key=lambda kv: kv[1][1])
+    n_steps = args.steps
+    if dom[0].startswith("hs"):
+        ops = pst["hs_applied"] * np.mean([hs_ops(s) for s in systems]) * n_steps
+        work = "FP64 ops of the Hansen-Sengupta sweeps (per-box count from the system tables)"
+    elif dom[0] in ("eval", "eval64"):
+        ops = pst["eval64_boxes"] * np.mean([eval_ops(s) for s in systems]) * n_steps
+        work = "FP64 ops of the FP64 evaluations"
+    else:
+        ops = 0
+        work = "control kernels"
+    achieved = ops / (dom[1][1] * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": dom[0], "achieved": achieved, "peak": fp64_rate / 1e12,
+                "unit": "TFLOP/s (FP64 directed ops)", "frac": achieved / (fp64_rate / 1e12),
+                "traffic": None, "peak_source": "measured in this run: directed __dadd_rd/__dmul_ru probe",
+                "work": work, "kernel_share": dom[1][1] / sum(v[1] for v in ktimes.values()),
+                "avg_launch_ms": dom[1][1] / max(1, dom[1][0])}
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            b, t = oracle_sample(systems[:1], args.cpu_boxes)
+            cpu = {"value": b / t, "unit": "boxes/s", "cores": 1, "kind": "oracle",
+                   "sample": f"first {b} boxes (LIFO order) of the {args.workload} solve, serial, fesetround"}
+        out = {
+            "metric": "boxes/sec", "value": value, "unit": "boxes/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 (f32 prefilter)", "data": "synthetic",
+            "config": {"workload": desc, "systems_per_step": len(systems), "l2": "flushed (256 MB write) between steps",
+                       "parallelism": f"replicas x{world}"},
+            "systems_per_s": sys_per_s,
+            "boxes_per_step": boxes / args.steps,
+            "plain_fp64_path": {"value": b64 / float(np.sum(t64)), "unit": "boxes/s",
+                                "ms_per_step": 1e3 * float(np.mean(t64))},
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "roofline": roofline,
+            "measured_rates": {"fp64_directed_ops_per_s": fp64_rate, "fp32_directed_ops_per_s": fp32_rate},
+            "kernel_ms": {k: round(v[1], 4) for k, v in ktimes.items()},
+            "host_loop_ms_per_step": 1e3 * float(np.mean(prof_t)),
+            "clocks": ck,
+            "cpu_baseline": cpu,
+            "wall_s": wall,
+        }
+        print(json.dumps(out), flush=True)
+    plan.close()
+    if dist:
+        td.destroy_process_group()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="n6")
+    ap.add_argument("--impl", default="ivsolve")
+    ap.add_argument("--wave-children", type=int, default=0)
+    ap.add_argument("--cpu-boxes", type=int, default=600_000)
+    ap.add_argument("--ref-boxes", type=int, default=200_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    systems, desc = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, systems, desc, rank, world)
+        return
+    run_gpu(args, systems, desc, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * ivsolve.h -- C ABI of the GB300 (sm_103a) interval solver for bounded polynomial
+ * systems: interval branch-and-bound with Hansen-Sengupta contraction, after
+ * Lin & Chen, "An efficient algorithm for global interval solution of nonlinear
+ * algebraic equations and its GPGPU implementation".
+ *
+ * Problem statement (Algorithm 1, In/Out): given polynomial equations f_1..f_m in
+ * x_1..x_n, a box of variable regions [d_lo_j, d_hi_j] and a desired width, return
+ * the boxes ("configurations") of that width that may contain a real solution.  Every
+ * real solution in the initial box lies in some returned box; an empty result with
+ * IVS_OK proves that the box holds no solution (Algorithm 1, termination (I)).
+ *
+ * Per box, in this order (each box's fate depends only on the box itself):
+ *   1. natural interval extension F(X) with outward rounding (Definition 1, eq 25-27);
+ *      drop the box if some F_i(X) does not contain 0 (Definition 2, Algorithm 2);
+ *   2. optional Hansen-Sengupta sweep (Section 2.3 eq 14, 17-22; Algorithm 3, with the
+ *      Gauss-Jordan preconditioner of Section 2.4 and the products of Algorithm 4);
+ *      drop the box if the sweep returns the empty set;
+ *   3. accept when max_j (hi_j - lo_j) <= tol (Algorithm 1 termination (II)), else split
+ *      every coordinate at its midpoint into 2^n children (Algorithm 2).
+ * Readings of garbled or silent passages are documented with the implementation.
+ *
+ * All pointers are HOST pointers unless stated.  Inputs are borrowed for the duration
+ * of the call and copied.  Results are owned by the library until ivs_result_free /
+ * ivs_plan_destroy.  Every function returns an int status (IVS_OK on success) unless
+ * it returns a count; no function aborts the process.  A GPU is required: with no
+ * device or no driver the calls return IVS_ERR_CUDA.
+ */
+#ifndef IVSOLVE_H
+#define IVSOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define IVS_OK 0
+#define IVS_ERR_INVALID 1  /* n <= 0 or > 16; lo > hi; non-finite input; exponent > 15;
+                              HS requested with m != n; bad option values          */
+#define IVS_ERR_NOMEM 2    /* device or host allocation failed, or the work queue
+                              cannot hold the boxes a step needs                    */
+#define IVS_ERR_BUDGET 3   /* max_boxes, max_results or max_depth was hit: the result
+                              is returned but flagged incomplete                    */
+#define IVS_ERR_TIMEOUT 4  /* time_budget_s elapsed; result incomplete              */
+#define IVS_ERR_CUDA 5     /* a CUDA call failed (message: ivs_last_error())        */
+
+/* ---- per-box flags of accepted boxes ------------------------------------------ */
+#define IVS_BOX_WIDTH 1          /* max width <= tol                                 */
+#define IVS_BOX_UNSPLITTABLE 2   /* widest coordinate cannot be split in doubles     */
+#define IVS_BOX_DEPTH_LIMIT 4    /* returned unsplit at max_depth (status BUDGET)    */
+
+/* Sparse monomial system (the paper's equations with "integer or floating number
+ * coefficients", Section 3.2).  Equation i owns terms [eq_offsets[i], eq_offsets[i+1]);
+ * term t is [coef_lo[t], coef_hi[t]] * prod_j x_j^exps[t*n_vars + j].  A coefficient
+ * that is not a double is given as the interval of the two doubles around it
+ * (coef_hi may be NULL when every coefficient is exact: then coef_hi = coef_lo).
+ * Limits: 1 <= n_vars <= 16, exponents <= 15, n_eqs >= 1. */
+typedef struct ivs_system {
+    int32_t n_vars, n_eqs, n_terms;
+    const int32_t *eq_offsets;   /* n_eqs + 1 entries, eq_offsets[0] == 0             */
+    const double *coef_lo;       /* n_terms                                           */
+    const double *coef_hi;       /* n_terms or NULL                                   */
+    const uint8_t *exps;         /* n_terms * n_vars, row-major                       */
+} ivs_system;
+
+typedef struct ivs_options {
+    double tol;              /* accept width (>= 0)                                   */
+    int32_t hs_enable;       /* 1: Hansen-Sengupta sweep on boxes that survive F(X)    */
+    int32_t hs_min_depth;    /* sweep only at depth >= this (the paper starts late)    */
+    int32_t hs_iters;        /* sweeps per visit (>= 1)                                */
+    int32_t prefilter_fp32;  /* 1: FP32 outward-rounded exclusion before FP64; it can
+                                only drop boxes FP64 drops, so results are identical   */
+    int32_t root_depth;      /* depth of the initial box                               */
+    int32_t max_depth;       /* a box that would split past it is returned with
+                                IVS_BOX_DEPTH_LIMIT and status IVS_ERR_BUDGET          */
+    int64_t max_boxes;       /* work budget in processed boxes, 0 = unlimited          */
+    int64_t max_results;     /* accepted-box capacity, 0 = library default             */
+    double time_budget_s;    /* wall-clock budget, 0 = unlimited                       */
+} ivs_options;
+
+typedef struct ivs_stats {
+    int64_t boxes;              /* boxes processed (each of the 2^n children counts)   */
+    int64_t excluded_prefilter; /* dropped by the FP32 stage                           */
+    int64_t excluded_eval;      /* dropped by the FP64 evaluation                      */
+    int64_t hs_applied;         /* HS sweeps run                                       */
+    int64_t hs_empty;           /* dropped by an HS sweep                              */
+    int64_t hs_contracted;      /* HS sweeps that changed the box                      */
+    int64_t hs_singular;        /* HS skipped (mid J singular, or B non-finite)        */
+    int64_t accepted;
+    int64_t unsplittable;
+    int64_t split;
+    int32_t max_depth_seen;
+    int32_t waves;              /* device sweeps over the queue                        */
+    double device_ms;           /* device time of the solve                            */
+    int64_t launches;           /* kernels the solve launched                          */
+    int64_t eval64_boxes;       /* boxes that ran the FP64 evaluation                  */
+} ivs_stats;
+
+typedef struct ivs_result ivs_result;
+typedef struct ivs_plan ivs_plan;
+
+/* Fills *o with defaults: tol 1e-6, HS on from depth 0, one sweep, FP32 prefilter on,
+ * root_depth 0, max_depth 200, no box or time budget. */
+void ivs_options_default(ivs_options *o);
+
+/* Solve one system on the initial box [box_lo, box_hi] (n_vars doubles each).
+ * On IVS_OK / IVS_ERR_BUDGET / IVS_ERR_TIMEOUT *out receives a result (free it with
+ * ivs_result_free); on other errors *out is NULL. */
+int ivs_solve(const ivs_system *sys, const double *box_lo, const double *box_hi,
+              const ivs_options *opt, ivs_result **out);
+
+/* Solve n_sys independent systems in one device run (batching form: the queues of all
+ * systems share every sweep).  box_lo[s] / box_hi[s] point to system s's box; opts is
+ * one options struct per system (or a single struct when opts_stride == 0).
+ * outs[s] receives system s's result.  Returns the first non-OK status among systems
+ * (or an error of the run itself). */
+int ivs_solve_batch(int32_t n_sys, const ivs_system *systems, const double *const *box_lo,
+                    const double *const *box_hi, const ivs_options *opts, int32_t opts_stride,
+                    ivs_result **outs);
+
+int64_t ivs_result_count(const ivs_result *r);
+int32_t ivs_result_n_vars(const ivs_result *r);
+int ivs_result_status(const ivs_result *r);
+/* Copies the accepted boxes, sorted lexicographically by (lo_0, hi_0, lo_1, ...),
+ * -0 written as +0.  lo, hi: count * n_vars doubles (row-major); flags, depth: count
+ * int32 each; any of them may be NULL. */
+int ivs_result_boxes(const ivs_result *r, double *lo, double *hi, int32_t *flags, int32_t *depth);
+int ivs_result_stats(const ivs_result *r, ivs_stats *st);
+void ivs_result_free(ivs_result *r);
+
+/* ---- device-resident plan: upload once, solve many times ---------------------- */
+/* cfg fields left 0 take defaults.  workspace: optional caller-owned DEVICE buffer
+ * (e.g. from a PyTorch allocation) of workspace_bytes; when NULL the plan allocates
+ * its own with cudaMalloc.  stream: a cudaStream_t (NULL = the plan creates one). */
+typedef struct ivs_plan_cfg {
+    void *workspace;
+    size_t workspace_bytes;
+    void *stream;
+    int64_t wave_children;   /* max children evaluated per sweep (0 = default)       */
+    int32_t eval_blocks;     /* grid of the evaluation kernel (0 = auto)             */
+    int32_t eval_threads;    /* block of the evaluation kernel (0 = auto)            */
+    int32_t device;          /* CUDA device ordinal                                  */
+    int32_t profile;         /* 1: time each kernel class with CUDA events           */
+} ivs_plan_cfg;
+
+/* Bytes of device workspace a plan with these systems needs for the given
+ * wave_children and queue capacity (queue_parents boxes).  Lets a caller allocate. */
+size_t ivs_workspace_bytes(int32_t n_sys, const ivs_system *systems, int64_t wave_children,
+                           int64_t queue_parents, int64_t max_results);
+
+int ivs_plan_create(int32_t n_sys, const ivs_system *systems, const double *const *box_lo,
+                    const double *const *box_hi, const ivs_options *opts, int32_t opts_stride,
+                    const ivs_plan_cfg *cfg, ivs_plan **out);
+/* Runs a full solve of every system in the plan on the plan's stream and waits for it.
+ * The plan's results are replaced on each run. */
+int ivs_plan_run(ivs_plan *p);
+/* Copies system s's result of the last run to the host. */
+int ivs_plan_result(ivs_plan *p, int32_t s, ivs_result **out);
+int ivs_plan_stats(ivs_plan *p, ivs_stats *st);   /* totals over all systems, last run */
+void ivs_plan_destroy(ivs_plan *p);
+
+/* Per-kernel-class device time of the last run of a plan created with cfg.profile = 1
+ * (CUDA events on the plan's stream around each launch).  Writes up to max entries and
+ * returns how many classes exist.  Class names: "eval", "hs_n<k>", "control". */
+typedef struct ivs_kernel_time {
+    char name[24];
+    int64_t launches;
+    double ms;
+} ivs_kernel_time;
+int32_t ivs_plan_kernel_times(ivs_plan *p, ivs_kernel_time *out, int32_t max);
+
+/* Microbenchmark of the directed-rounding arithmetic rate of the device (no paper
+ * counterpart; it supplies the roofline denominator): kind 0 = FP64 (__dadd_rd /
+ * __dmul_ru chains), kind 1 = FP32 (__fadd_rd / __fmul_ru).  Writes the rate in
+ * operations per second (one add or one multiply = one operation) and the kernel time. */
+int ivs_probe_rate(int32_t kind, int32_t device, double *ops_per_s, double *ms);
+
+const char *ivs_status_str(int status);
+const char *ivs_last_error(void);   /* thread-local text of the last error           */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IVSOLVE_H */

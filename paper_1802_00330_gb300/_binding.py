@@ -1,0 +1,275 @@
+"""ctypes binding of ``libivsolve.so`` (declared in ``include/ivsolve.h``).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA kernels.
+There is no CPU fallback -- if the library is missing or no GPU is present the calls
+raise.  Function names follow the C ABI; ``solve`` / ``solve_batch`` / ``Plan`` are thin
+conveniences that return numpy arrays.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libivsolve.so")
+
+IVS_OK, IVS_ERR_INVALID, IVS_ERR_NOMEM, IVS_ERR_BUDGET, IVS_ERR_TIMEOUT, IVS_ERR_CUDA = range(6)
+IVS_BOX_WIDTH, IVS_BOX_UNSPLITTABLE, IVS_BOX_DEPTH_LIMIT = 1, 2, 4
+
+
+class ivs_system(C.Structure):
+    _fields_ = [("n_vars", C.c_int32), ("n_eqs", C.c_int32), ("n_terms", C.c_int32),
+                ("eq_offsets", C.c_void_p), ("coef_lo", C.c_void_p), ("coef_hi", C.c_void_p),
+                ("exps", C.c_void_p)]
+
+
+class ivs_options(C.Structure):
+    _fields_ = [("tol", C.c_double), ("hs_enable", C.c_int32), ("hs_min_depth", C.c_int32),
+                ("hs_iters", C.c_int32), ("prefilter_fp32", C.c_int32), ("root_depth", C.c_int32),
+                ("max_depth", C.c_int32), ("max_boxes", C.c_int64), ("max_results", C.c_int64),
+                ("time_budget_s", C.c_double)]
+
+
+class ivs_stats(C.Structure):
+    _fields_ = [("boxes", C.c_int64), ("excluded_prefilter", C.c_int64), ("excluded_eval", C.c_int64),
+                ("hs_applied", C.c_int64), ("hs_empty", C.c_int64), ("hs_contracted", C.c_int64),
+                ("hs_singular", C.c_int64), ("accepted", C.c_int64), ("unsplittable", C.c_int64),
+                ("split", C.c_int64), ("max_depth_seen", C.c_int32), ("waves", C.c_int32),
+                ("device_ms", C.c_double), ("launches", C.c_int64), ("eval64_boxes", C.c_int64)]
+
+
+class ivs_plan_cfg(C.Structure):
+    _fields_ = [("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t), ("stream", C.c_void_p),
+                ("wave_children", C.c_int64), ("eval_blocks", C.c_int32), ("eval_threads", C.c_int32),
+                ("device", C.c_int32), ("profile", C.c_int32)]
+
+
+class ivs_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("ms", C.c_double)]
+
+
+# name -> (restype, argtypes); the full list of entry points of include/ivsolve.h
+_VP = C.c_void_p
+_PP = C.POINTER(C.c_void_p)
+SIGNATURES = {
+    "ivs_options_default": (None, [C.POINTER(ivs_options)]),
+    "ivs_solve": (C.c_int, [C.POINTER(ivs_system), _VP, _VP, C.POINTER(ivs_options), _PP]),
+    "ivs_solve_batch": (C.c_int, [C.c_int32, C.POINTER(ivs_system), _VP, _VP, C.POINTER(ivs_options),
+                                  C.c_int32, _PP]),
+    "ivs_result_count": (C.c_int64, [_VP]),
+    "ivs_result_n_vars": (C.c_int32, [_VP]),
+    "ivs_result_status": (C.c_int, [_VP]),
+    "ivs_result_boxes": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "ivs_result_stats": (C.c_int, [_VP, C.POINTER(ivs_stats)]),
+    "ivs_result_free": (None, [_VP]),
+    "ivs_workspace_bytes": (C.c_size_t, [C.c_int32, C.POINTER(ivs_system), C.c_int64, C.c_int64, C.c_int64]),
+    "ivs_plan_create": (C.c_int, [C.c_int32, C.POINTER(ivs_system), _VP, _VP, C.POINTER(ivs_options),
+                                  C.c_int32, C.POINTER(ivs_plan_cfg), _PP]),
+    "ivs_plan_run": (C.c_int, [_VP]),
+    "ivs_plan_result": (C.c_int, [_VP, C.c_int32, _PP]),
+    "ivs_plan_stats": (C.c_int, [_VP, C.POINTER(ivs_stats)]),
+    "ivs_plan_destroy": (None, [_VP]),
+    "ivs_plan_kernel_times": (C.c_int32, [_VP, _VP, C.c_int32]),
+    "ivs_probe_rate": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "ivs_status_str": (C.c_char_p, [C.c_int]),
+    "ivs_last_error": (C.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Load the CUDA library; raises if it was not built (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "paper_1802_00330_gb300.build.build() (nvcc, sm_103a)")
+            lib = C.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def __getattr__(name):
+    if name in SIGNATURES:
+        return getattr(load(), name)
+    raise AttributeError(name)
+
+
+class IvsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def _check(rc):
+    if rc != IVS_OK:
+        lib = load()
+        raise IvsError(rc, f"{lib.ivs_status_str(rc).decode()}: {lib.ivs_last_error().decode()}")
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class _SysRef:
+    """Owns contiguous copies of a system's arrays while a C struct points at them."""
+
+    def __init__(self, s):
+        self.off = np.ascontiguousarray(s.eq_offsets, dtype=np.int32)
+        self.clo = np.ascontiguousarray(s.coef_lo, dtype=np.float64)
+        self.chi = np.ascontiguousarray(s.coef_hi, dtype=np.float64)
+        self.exps = np.ascontiguousarray(s.exps, dtype=np.uint8)
+        self.lo = np.ascontiguousarray(s.box_lo, dtype=np.float64)
+        self.hi = np.ascontiguousarray(s.box_hi, dtype=np.float64)
+        self.c = ivs_system(int(s.n_vars), int(s.n_eqs), int(self.off[-1]), _ptr(self.off),
+                            _ptr(self.clo), _ptr(self.chi), _ptr(self.exps))
+
+
+def make_options(tol=1e-6, hs_enable=True, hs_min_depth=0, hs_iters=1, prefilter_fp32=True,
+                 root_depth=0, max_depth=200, max_boxes=0, max_results=0, time_budget_s=0.0):
+    o = ivs_options()
+    load().ivs_options_default(C.byref(o))
+    o.tol = float(tol)
+    o.hs_enable = int(hs_enable)
+    o.hs_min_depth = int(hs_min_depth)
+    o.hs_iters = int(hs_iters)
+    o.prefilter_fp32 = int(prefilter_fp32)
+    o.root_depth = int(root_depth)
+    o.max_depth = int(max_depth)
+    o.max_boxes = int(max_boxes)
+    o.max_results = int(max_results)
+    o.time_budget_s = float(time_budget_s)
+    return o
+
+
+def result_to_dict(r):
+    lib = load()
+    cnt = lib.ivs_result_count(r)
+    n = lib.ivs_result_n_vars(r)
+    lo = np.zeros((cnt, n))
+    hi = np.zeros((cnt, n))
+    flags = np.zeros(cnt, np.int32)
+    depth = np.zeros(cnt, np.int32)
+    _check(lib.ivs_result_boxes(r, _ptr(lo), _ptr(hi), _ptr(flags), _ptr(depth)))
+    st = ivs_stats()
+    _check(lib.ivs_result_stats(r, C.byref(st)))
+    return {"status": lib.ivs_result_status(r), "lo": lo, "hi": hi, "flags": flags, "depth": depth,
+            "stats": {k: getattr(st, k) for k, _ in ivs_stats._fields_}}
+
+
+def solve(s, box_lo=None, box_hi=None, **opts):
+    """Solve one system (a ``synth.PolySystem``-like object) through ``ivs_solve``."""
+    lib = load()
+    ref = _SysRef(s)
+    lo = ref.lo if box_lo is None else np.ascontiguousarray(box_lo, dtype=np.float64)
+    hi = ref.hi if box_hi is None else np.ascontiguousarray(box_hi, dtype=np.float64)
+    opts.setdefault("tol", s.tol)
+    o = make_options(**opts)
+    res = C.c_void_p()
+    rc = lib.ivs_solve(C.byref(ref.c), _ptr(lo), _ptr(hi), C.byref(o), C.byref(res))
+    if not res:
+        _check(rc)
+    try:
+        return result_to_dict(res)
+    finally:
+        lib.ivs_result_free(res)
+
+
+class Plan:
+    """Device-resident plan over one or more systems (``ivs_plan_*``).  ``workspace`` may
+    be a CUDA tensor (e.g. ``torch.empty(nbytes, dtype=torch.uint8, device='cuda')``) that
+    the plan uses instead of allocating; ``stream`` a ``torch.cuda.Stream``."""
+
+    def __init__(self, systems, opts=None, wave_children=0, workspace=None, workspace_bytes=0,
+                 stream=None, eval_blocks=0, eval_threads=0, profile=False):
+        lib = load()
+        self._lib = lib
+        self.refs = [_SysRef(s) for s in systems]
+        self.n_sys = len(systems)
+        arr = (ivs_system * self.n_sys)(*[r.c for r in self.refs])
+        los = (C.c_void_p * self.n_sys)(*[_ptr(r.lo) for r in self.refs])
+        his = (C.c_void_p * self.n_sys)(*[_ptr(r.hi) for r in self.refs])
+        if opts is None:
+            opts = [make_options(tol=s.tol) for s in systems]
+        elif isinstance(opts, dict):
+            opts = [make_options(**{"tol": s.tol, **opts}) for s in systems]
+        oarr = (ivs_options * self.n_sys)(*opts)
+        cfg = ivs_plan_cfg()
+        self._workspace = workspace
+        if workspace is not None:
+            cfg.workspace = C.c_void_p(int(workspace.data_ptr()))
+            cfg.workspace_bytes = int(workspace.numel() * workspace.element_size())
+        else:
+            cfg.workspace_bytes = int(workspace_bytes)
+        if stream is not None:
+            cfg.stream = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        cfg.wave_children = int(wave_children)
+        cfg.eval_blocks = int(eval_blocks)
+        cfg.eval_threads = int(eval_threads)
+        cfg.profile = int(profile)
+        self.p = C.c_void_p()
+        _check(lib.ivs_plan_create(self.n_sys, arr, los, his, oarr, C.sizeof(ivs_options), C.byref(cfg),
+                                   C.byref(self.p)))
+
+    def run(self):
+        rc = self._lib.ivs_plan_run(self.p)
+        if rc not in (IVS_OK, IVS_ERR_TIMEOUT, IVS_ERR_NOMEM):
+            _check(rc)
+        return rc
+
+    def stats(self):
+        st = ivs_stats()
+        _check(self._lib.ivs_plan_stats(self.p, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ivs_stats._fields_}
+
+    def result(self, s=0):
+        res = C.c_void_p()
+        _check(self._lib.ivs_plan_result(self.p, int(s), C.byref(res)))
+        try:
+            return result_to_dict(res)
+        finally:
+            self._lib.ivs_result_free(res)
+
+    def kernel_times(self):
+        arr = (ivs_kernel_time * 64)()
+        k = self._lib.ivs_plan_kernel_times(self.p, arr, 64)
+        return {arr[q].name.decode(): (arr[q].launches, arr[q].ms) for q in range(min(k, 64))}
+
+    def close(self):
+        if self.p:
+            self._lib.ivs_plan_destroy(self.p)
+            self.p = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def probe_rate(kind=0, device=0):
+    """Measured directed-rounding rate of the device in ops/s (kind 0 FP64, 1 FP32)."""
+    ops = C.c_double()
+    ms = C.c_double()
+    _check(load().ivs_probe_rate(int(kind), int(device), C.byref(ops), C.byref(ms)))
+    return ops.value, ms.value
+
+
+def solve_batch(systems, **opts):
+    plan = Plan(systems, opts=opts or None)
+    try:
+        plan.run()
+        return [plan.result(s) for s in range(len(systems))]
+    finally:
+        plan.close()

@@ -1,0 +1,698 @@
+// ivs_host.cu -- host runtime behind include/ivsolve.h: input validation, compilation of
+// each system into device tables (F and its Jacobian), the device workspace, the sweep
+// loop over the device queue, and result collection.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ivsolve.h"
+#include "ivs_internal.h"
+#include "ivs_kernels.cuh"
+
+using namespace ivs;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int status, const std::string &msg) {
+    g_last_error = msg;
+    return status;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(IVS_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// ---- outward rounding on the host (exact, from an error-free product) --------------
+// p = RN(c * a); e = fma(c, a, -p) is the exact error (Dekker/Ogita-Rump-Oishi
+// TwoProduct), so the rounded-down product is p when e >= 0 and the next double below p
+// otherwise; symmetric for rounding up.
+double mul_down(double c, double a) {
+    double p = c * a;
+    double e = std::fma(c, a, -p);
+    return e < 0 ? std::nextafter(p, -INFINITY) : p;
+}
+double mul_up(double c, double a) {
+    double p = c * a;
+    double e = std::fma(c, a, -p);
+    return e > 0 ? std::nextafter(p, INFINITY) : p;
+}
+float to_float_down(double d) {
+    float f = (float)d;
+    if ((double)f > d) f = std::nextafter(f, -INFINITY);
+    return f;
+}
+float to_float_up(double d) {
+    float f = (float)d;
+    if ((double)f < d) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+struct HostTables {
+    std::vector<DevSys> sys;
+    std::vector<int32_t> poly_term_off{0};
+    std::vector<double> clo, chi;
+    std::vector<float> clo32, chi32;
+    std::vector<int32_t> fac_off{0};
+    std::vector<uint8_t> fac;
+};
+
+void add_term(HostTables &h, double clo, double chi, const uint8_t *e, int n) {
+    h.clo.push_back(clo);
+    h.chi.push_back(chi);
+    h.clo32.push_back(to_float_down(clo));
+    h.chi32.push_back(to_float_up(chi));
+    for (int j = 0; j < n; j++)
+        if (e[j]) h.fac.push_back((uint8_t)((j << 4) | e[j]));
+    h.fac_off.push_back((int32_t)h.fac.size());
+}
+
+int validate(const ivs_system *s, const double *lo, const double *hi, const ivs_options *o) {
+    if (!s || !lo || !hi || !o) return fail(IVS_ERR_INVALID, "null argument");
+    if (s->n_vars <= 0 || s->n_vars > kMaxVars) return fail(IVS_ERR_INVALID, "n_vars must be in 1..16");
+    if (s->n_eqs <= 0 || s->n_terms < 0) return fail(IVS_ERR_INVALID, "n_eqs must be >= 1, n_terms >= 0");
+    if (!s->eq_offsets || (s->n_terms > 0 && (!s->coef_lo || !s->exps)))
+        return fail(IVS_ERR_INVALID, "null system array");
+    if (s->eq_offsets[0] != 0 || s->eq_offsets[s->n_eqs] != s->n_terms)
+        return fail(IVS_ERR_INVALID, "eq_offsets must run from 0 to n_terms");
+    for (int i = 0; i < s->n_eqs; i++)
+        if (s->eq_offsets[i + 1] < s->eq_offsets[i]) return fail(IVS_ERR_INVALID, "eq_offsets not monotone");
+    for (int t = 0; t < s->n_terms; t++) {
+        double a = s->coef_lo[t], b = s->coef_hi ? s->coef_hi[t] : a;
+        if (!std::isfinite(a) || !std::isfinite(b) || a > b) return fail(IVS_ERR_INVALID, "bad coefficient");
+        for (int j = 0; j < s->n_vars; j++)
+            if (s->exps[(size_t)t * s->n_vars + j] > kMaxExp) return fail(IVS_ERR_INVALID, "exponent > 15");
+    }
+    for (int j = 0; j < s->n_vars; j++)
+        if (!std::isfinite(lo[j]) || !std::isfinite(hi[j]) || lo[j] > hi[j])
+            return fail(IVS_ERR_INVALID, "bad initial box");
+    if (o->hs_enable && s->n_eqs != s->n_vars) return fail(IVS_ERR_INVALID, "HS needs n_eqs == n_vars");
+    if (!(o->tol >= 0) || !std::isfinite(o->tol)) return fail(IVS_ERR_INVALID, "tol must be finite and >= 0");
+    if (o->hs_iters < 0 || o->max_depth < 0 || o->max_depth > 0xFFF0 || o->root_depth < 0 ||
+        o->root_depth > o->max_depth)
+        return fail(IVS_ERR_INVALID, "bad depth / iteration options");
+    return IVS_OK;
+}
+
+// F_i and J_ij polynomials of one system appended to the tables.  J_ij = sum over terms t
+// of equation i with a_tj > 0 of [down(c_lo a_tj), up(c_hi a_tj)] x^(a_t - e_j), in term
+// order; its factors keep the variable order of the term.
+void compile_system(HostTables &h, const ivs_system *s, const ivs_options *o) {
+    const int n = s->n_vars, m = s->n_eqs;
+    DevSys d{};
+    d.n = n;
+    d.m = m;
+    d.f_poly = (int32_t)h.poly_term_off.size() - 1;
+    for (int i = 0; i < m; i++) {
+        for (int t = s->eq_offsets[i]; t < s->eq_offsets[i + 1]; t++) {
+            double clo = s->coef_lo[t], chi = s->coef_hi ? s->coef_hi[t] : clo;
+            add_term(h, clo, chi, s->exps + (size_t)t * n, n);
+        }
+        h.poly_term_off.push_back((int32_t)h.clo.size());
+    }
+    d.j_poly = -1;
+    if (m == n) {
+        d.j_poly = (int32_t)h.poly_term_off.size() - 1;
+        uint8_t e[kMaxVars];
+        for (int i = 0; i < m; i++)
+            for (int j = 0; j < n; j++) {
+                for (int t = s->eq_offsets[i]; t < s->eq_offsets[i + 1]; t++) {
+                    const uint8_t *a = s->exps + (size_t)t * n;
+                    if (a[j] == 0) continue;
+                    double clo = s->coef_lo[t], chi = s->coef_hi ? s->coef_hi[t] : clo;
+                    std::memcpy(e, a, (size_t)n);
+                    e[j] -= 1;
+                    add_term(h, mul_down(clo, (double)a[j]), mul_up(chi, (double)a[j]), e, n);
+                }
+                h.poly_term_off.push_back((int32_t)h.clo.size());
+            }
+    }
+    d.tol = o->tol + 0.0;   // -0 -> +0
+    d.hs_enable = o->hs_enable ? 1 : 0;
+    d.hs_min_depth = o->hs_min_depth;
+    d.hs_iters = o->hs_iters > 0 ? o->hs_iters : 1;
+    d.max_depth = o->max_depth;
+    d.prefilter = o->prefilter_fp32 ? 1 : 0;
+    d.max_boxes = o->max_boxes;
+    h.sys.push_back(d);
+}
+
+}  // namespace
+
+struct ivs_result {
+    int status = IVS_OK;
+    int n = 0;
+    std::vector<double> lo, hi;
+    std::vector<int32_t> flags, depth;
+    ivs_stats st{};
+};
+
+struct ivs_plan {
+    int n_sys = 0, n_max = 0, device = 0, num_sms = 0;
+    int eval_blocks = 0, eval_threads = 256;
+    std::vector<int> dims;                 // distinct n over systems (HS kernels to launch)
+    std::vector<ivs_options> opts;
+    std::vector<int> sys_n;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *ws = nullptr;
+    bool own_ws = false;
+    void *tables_mem = nullptr;
+    SweepArgs args{};
+    int64_t wave_children = 0, queue_cap = 0, out_cap = 0;
+    double *d_box_lo = nullptr, *d_box_hi = nullptr;
+    int32_t *d_root_depth = nullptr;
+    WaveCtl *h_ctl = nullptr;              // pinned
+    std::vector<unsigned long long> h_stats;
+    int run_status = IVS_OK;
+    float last_ms = 0.f;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double time_budget_s = 0;
+    int64_t launches = 0;
+    // profiling: stage events of one sweep and accumulated times per kernel class
+    bool profile = false;
+    std::vector<cudaEvent_t> stage_ev;
+    std::vector<double> class_ms;          // [0] eval, [1] control, [2] eval64, [3 + q] hs dim q
+    std::vector<int64_t> class_launches;
+    // graph path: the whole sweep loop as one conditional-WHILE graph
+    bool use_graph = true;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t *h_wave_limit = nullptr;       // pinned
+};
+
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+    size_t queue, stage, surv, out, ctl, stats, roots, total;
+};
+
+Layout layout_for(int n_sys, int n_max, int64_t W, int64_t Q, int64_t O) {
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    L.queue = take((size_t)Q * (3 * n_max * sizeof(double) + 2 * sizeof(int32_t)) + 4 * 256);
+    L.stage = take((size_t)W * (3 * n_max * sizeof(double) + 2 * sizeof(int32_t)) + 4 * 256);
+    L.surv = take((size_t)(n_max + 2) * W * sizeof(Surv));
+    L.out = take((size_t)O * (2 * n_max * sizeof(double) + 3 * sizeof(int32_t)) + 4 * 256);
+    L.ctl = take(sizeof(WaveCtl));
+    L.stats = take((size_t)n_sys * ST_COUNT * sizeof(unsigned long long));
+    L.roots = take((size_t)n_sys * (2 * n_max * sizeof(double) + sizeof(int32_t)) + 2 * 256);
+    L.total = off;
+    return L;
+}
+
+DevQueue carve_queue(char *base, int64_t cap, int n_max) {
+    DevQueue q{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char *p = base + off; off = align_up(off + bytes, 256); return p; };
+    q.lo = (double *)take((size_t)cap * n_max * sizeof(double));
+    q.mid = (double *)take((size_t)cap * n_max * sizeof(double));
+    q.hi = (double *)take((size_t)cap * n_max * sizeof(double));
+    q.sys = (int32_t *)take((size_t)cap * sizeof(int32_t));
+    q.meta = (uint32_t *)take((size_t)cap * sizeof(uint32_t));
+    q.cap = cap;
+    return q;
+}
+
+DevOut carve_out(char *base, int64_t cap, int n_max) {
+    DevOut o{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char *p = base + off; off = align_up(off + bytes, 256); return p; };
+    o.lo = (double *)take((size_t)cap * n_max * sizeof(double));
+    o.hi = (double *)take((size_t)cap * n_max * sizeof(double));
+    o.sys = (int32_t *)take((size_t)cap * sizeof(int32_t));
+    o.flags = (int32_t *)take((size_t)cap * sizeof(int32_t));
+    o.depth = (int32_t *)take((size_t)cap * sizeof(int32_t));
+    o.cap = cap;
+    return o;
+}
+
+template <class T>
+int upload(void *&cursor, const std::vector<T> &v, const T *&dst, cudaStream_t st) {
+    dst = reinterpret_cast<const T *>(cursor);
+    if (!v.empty()) CUDA_TRY(cudaMemcpyAsync(cursor, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    cursor = (char *)cursor + align_up(std::max<size_t>(v.size() * sizeof(T), 1), 256);
+    return IVS_OK;
+}
+
+const ivs_options *opt_at(const ivs_options *opts, int32_t stride, int s) {
+    return stride == 0 ? opts : (const ivs_options *)((const char *)opts + (size_t)stride * s);
+}
+
+}  // namespace
+
+extern "C" {
+
+void ivs_options_default(ivs_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tol = 1e-6;
+    o->hs_enable = 1;
+    o->hs_min_depth = 0;
+    o->hs_iters = 1;
+    o->prefilter_fp32 = 1;
+    o->root_depth = 0;
+    o->max_depth = 200;
+    o->max_boxes = 0;
+    o->max_results = 0;
+    o->time_budget_s = 0;
+}
+
+const char *ivs_status_str(int s) {
+    switch (s) {
+    case IVS_OK: return "ok";
+    case IVS_ERR_INVALID: return "invalid argument";
+    case IVS_ERR_NOMEM: return "out of memory";
+    case IVS_ERR_BUDGET: return "budget exhausted (result incomplete)";
+    case IVS_ERR_TIMEOUT: return "time budget exhausted (result incomplete)";
+    case IVS_ERR_CUDA: return "CUDA error";
+    default: return "unknown status";
+    }
+}
+
+const char *ivs_last_error(void) { return g_last_error.c_str(); }
+
+size_t ivs_workspace_bytes(int32_t n_sys, const ivs_system *systems, int64_t W, int64_t Q, int64_t O) {
+    int n_max = 1;
+    for (int s = 0; s < n_sys; s++) n_max = std::max(n_max, (int)systems[s].n_vars);
+    return layout_for(n_sys, n_max, W, Q, O).total;
+}
+
+void ivs_plan_destroy(ivs_plan *p) {
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    if (p->own_ws && p->ws) cudaFree(p->ws);
+    if (p->tables_mem) cudaFree(p->tables_mem);
+    if (p->h_ctl) cudaFreeHost(p->h_ctl);
+    if (p->ev0) cudaEventDestroy(p->ev0);
+    if (p->ev1) cudaEventDestroy(p->ev1);
+    for (cudaEvent_t e : p->stage_ev) cudaEventDestroy(e);
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->h_wave_limit) cudaFreeHost(p->h_wave_limit);
+    if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+    delete p;
+}
+
+int ivs_plan_create(int32_t n_sys, const ivs_system *systems, const double *const *box_lo,
+                    const double *const *box_hi, const ivs_options *opts, int32_t opts_stride,
+                    const ivs_plan_cfg *cfg, ivs_plan **out) {
+    if (!out) return fail(IVS_ERR_INVALID, "null out");
+    *out = nullptr;
+    if (n_sys <= 0 || !systems || !box_lo || !box_hi || !opts) return fail(IVS_ERR_INVALID, "bad arguments");
+    ivs_plan_cfg c{};
+    if (cfg) c = *cfg;
+    std::unique_ptr<ivs_plan, void (*)(ivs_plan *)> p(new (std::nothrow) ivs_plan(), ivs_plan_destroy);
+    if (!p) return fail(IVS_ERR_NOMEM, "host allocation");
+    p->n_sys = n_sys;
+    HostTables h;
+    int64_t out_cap = 0;
+    std::vector<double> roots_lo, roots_hi;
+    std::vector<int32_t> root_depth;
+    for (int s = 0; s < n_sys; s++) {
+        const ivs_options *o = opt_at(opts, opts_stride, s);
+        int rc = validate(&systems[s], box_lo[s], box_hi[s], o);
+        if (rc) return fail(rc, "system " + std::to_string(s) + ": " + g_last_error);
+        p->n_max = std::max(p->n_max, (int)systems[s].n_vars);
+        out_cap += o->max_results > 0 ? o->max_results : 0;
+        p->opts.push_back(*o);
+        p->sys_n.push_back(systems[s].n_vars);
+        if (std::find(p->dims.begin(), p->dims.end(), systems[s].n_vars) == p->dims.end())
+            p->dims.push_back(systems[s].n_vars);
+        compile_system(h, &systems[s], o);
+        if (o->time_budget_s > 0)
+            p->time_budget_s = p->time_budget_s > 0 ? std::min(p->time_budget_s, o->time_budget_s) : o->time_budget_s;
+    }
+    std::sort(p->dims.begin(), p->dims.end());
+    for (int s = 0; s < n_sys; s++) {
+        for (int j = 0; j < p->n_max; j++) {
+            bool in = j < systems[s].n_vars;
+            roots_lo.push_back(in ? box_lo[s][j] : 0.0);
+            roots_hi.push_back(in ? box_hi[s][j] : 0.0);
+        }
+        root_depth.push_back(opt_at(opts, opts_stride, s)->root_depth);
+    }
+    if (out_cap <= 0) out_cap = std::max<int64_t>(1 << 20, (int64_t)n_sys * 4096);
+
+    p->device = c.device;
+    CUDA_TRY(cudaSetDevice(p->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+    if (c.stream) {
+        p->stream = (cudaStream_t)c.stream;
+    } else {
+        CUDA_TRY(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
+        p->own_stream = true;
+    }
+    CUDA_TRY(cudaEventCreate(&p->ev0));
+    CUDA_TRY(cudaEventCreate(&p->ev1));
+    CUDA_TRY(cudaMallocHost((void **)&p->h_ctl, sizeof(WaveCtl)));
+
+    // workspace: wave size W, queue capacity Q, result capacity O
+    const int64_t W = c.wave_children > 0 ? c.wave_children : (int64_t)1 << 22;
+    int64_t Q;
+    size_t fixed = layout_for(n_sys, p->n_max, W, 0, out_cap).total;
+    const size_t per_parent = 3 * p->n_max * sizeof(double) + 2 * sizeof(int32_t);
+    if (c.workspace) {
+        if (c.workspace_bytes <= fixed + 64 * 1024) return fail(IVS_ERR_NOMEM, "workspace too small");
+        Q = (int64_t)((c.workspace_bytes - fixed - 64 * 1024) / per_parent);
+        p->ws = c.workspace;
+    } else {
+        size_t want = c.workspace_bytes > 0 ? c.workspace_bytes : fixed + per_parent * (size_t)(4 * W) + (1 << 20);
+        Q = (int64_t)((want - fixed - 64 * 1024) / per_parent);
+        if (Q < 16) return fail(IVS_ERR_NOMEM, "workspace too small");
+        size_t total = layout_for(n_sys, p->n_max, W, Q, out_cap).total;
+        cudaError_t e = cudaMalloc(&p->ws, total);
+        if (e != cudaSuccess) return fail(IVS_ERR_NOMEM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
+        p->own_ws = true;
+    }
+    if (Q < n_sys) return fail(IVS_ERR_NOMEM, "queue cannot hold the initial boxes");
+    Layout L = layout_for(n_sys, p->n_max, W, Q, out_cap);
+    char *ws = (char *)p->ws;
+    SweepArgs &a = p->args;
+    a.q = carve_queue(ws + L.queue, Q, p->n_max);
+    a.stage = carve_queue(ws + L.stage, W, p->n_max);
+    a.surv = (Surv *)(ws + L.surv);
+    a.surv_cap = W;
+    a.cand = a.surv + (size_t)(p->n_max + 1) * W;
+    a.out = carve_out(ws + L.out, out_cap, p->n_max);
+    a.ctl = (WaveCtl *)(ws + L.ctl);
+    a.stats = (unsigned long long *)(ws + L.stats);
+    a.wave_children = W;
+    a.max_fan_shift = p->n_max;
+    a.n_sys = n_sys;
+    p->d_box_lo = (double *)(ws + L.roots);
+    p->d_box_hi = p->d_box_lo + (size_t)n_sys * p->n_max;
+    p->d_root_depth = (int32_t *)(p->d_box_hi + (size_t)n_sys * p->n_max);
+    p->wave_children = W;
+    p->queue_cap = Q;
+    p->out_cap = out_cap;
+
+    // tables
+    size_t tbytes = 0;
+    auto acc = [&](size_t b) { tbytes += align_up(std::max<size_t>(b, 1), 256); };
+    acc(h.sys.size() * sizeof(DevSys));
+    acc(h.poly_term_off.size() * 4);
+    acc(h.clo.size() * 8);
+    acc(h.chi.size() * 8);
+    acc(h.clo32.size() * 4);
+    acc(h.chi32.size() * 4);
+    acc(h.fac_off.size() * 4);
+    acc(h.fac.size());
+    CUDA_TRY(cudaMalloc(&p->tables_mem, tbytes));
+    void *cur = p->tables_mem;
+    int rc = 0;
+    if ((rc = upload(cur, h.sys, a.tb.sys, p->stream)) || (rc = upload(cur, h.poly_term_off, a.tb.poly_term_off, p->stream)) ||
+        (rc = upload(cur, h.clo, a.tb.term_clo, p->stream)) || (rc = upload(cur, h.chi, a.tb.term_chi, p->stream)) ||
+        (rc = upload(cur, h.clo32, a.tb.term_clo32, p->stream)) || (rc = upload(cur, h.chi32, a.tb.term_chi32, p->stream)) ||
+        (rc = upload(cur, h.fac_off, a.tb.term_fac_off, p->stream)) || (rc = upload(cur, h.fac, a.tb.fac, p->stream)))
+        return rc;
+    CUDA_TRY(cudaMemcpyAsync(p->d_box_lo, roots_lo.data(), roots_lo.size() * 8, cudaMemcpyHostToDevice, p->stream));
+    CUDA_TRY(cudaMemcpyAsync(p->d_box_hi, roots_hi.data(), roots_hi.size() * 8, cudaMemcpyHostToDevice, p->stream));
+    CUDA_TRY(cudaMemcpyAsync(p->d_root_depth, root_depth.data(), root_depth.size() * 4, cudaMemcpyHostToDevice, p->stream));
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+
+    p->eval_threads = c.eval_threads > 0 ? c.eval_threads : 256;
+    p->eval_blocks = c.eval_blocks > 0 ? c.eval_blocks : p->num_sms * 8;
+    p->h_stats.assign((size_t)n_sys * ST_COUNT, 0);
+    p->profile = c.profile != 0;
+    if (p->profile) {
+        p->stage_ev.resize(p->dims.size() + 5);
+        for (auto &e : p->stage_ev) CUDA_TRY(cudaEventCreate(&e));
+    }
+    // profiling needs per-stage events, which a graph body cannot hold: host loop then
+    p->use_graph = !p->profile && std::getenv("IVS_HOST_LOOP") == nullptr;
+    if (p->use_graph) {
+        CUDA_TRY(cudaMallocHost((void **)&p->h_wave_limit, sizeof(int64_t)));
+        CUDA_TRY(build_sweep_graph(a, p->dims.data(), (int)p->dims.size(), p->eval_blocks, p->eval_threads,
+                                   p->num_sms, &p->graph));
+        CUDA_TRY(cudaGraphInstantiate(&p->graph_exec, p->graph, 0));
+    }
+    p->class_ms.assign(3 + p->dims.size(), 0.0);
+    p->class_launches.assign(3 + p->dims.size(), 0);
+    *out = p.release();
+    return IVS_OK;
+}
+
+int ivs_plan_run(ivs_plan *p) {
+    if (!p) return fail(IVS_ERR_INVALID, "null plan");
+    CUDA_TRY(cudaSetDevice(p->device));
+    SweepArgs &a = p->args;
+    cudaStream_t st = p->stream;
+    auto t0 = std::chrono::steady_clock::now();
+    CUDA_TRY(cudaEventRecord(p->ev0, st));
+    CUDA_TRY(cudaMemsetAsync(a.stats, 0, (size_t)p->n_sys * ST_COUNT * sizeof(unsigned long long), st));
+    CUDA_TRY(launch_seed_roots(a, p->d_box_lo, p->d_box_hi, p->d_root_depth, p->n_sys, p->n_max, st));
+    int status = IVS_OK;
+    const int nd = (int)p->dims.size();
+    std::fill(p->class_ms.begin(), p->class_ms.end(), 0.0);
+    std::fill(p->class_launches.begin(), p->class_launches.end(), 0);
+    p->launches = 1;
+    if (p->use_graph) {
+        // one graph launch runs sweeps until the queue is empty; with a time budget the
+        // loop is cut into chunks of sweeps so the host can check the clock in between
+        const int64_t chunk = p->time_budget_s > 0 ? 16 : ((int64_t)1 << 62);
+        int64_t waves_done = 0;
+        for (;;) {
+            *p->h_wave_limit = waves_done + chunk;
+            CUDA_TRY(cudaMemcpyAsync(&a.ctl->wave_limit, p->h_wave_limit, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+            CUDA_TRY(cudaGraphLaunch(p->graph_exec, st));
+            CUDA_TRY(cudaMemcpyAsync(p->h_ctl, a.ctl, sizeof(WaveCtl), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            p->launches += (5 + nd) * (p->h_ctl->waves - waves_done);
+            waves_done = p->h_ctl->waves;
+            if (p->h_ctl->error) { status = IVS_ERR_NOMEM; break; }
+            if (p->h_ctl->top == 0) break;
+            if (p->time_budget_s > 0) {
+                double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                if (el > p->time_budget_s) { status = IVS_ERR_TIMEOUT; break; }
+            }
+        }
+    } else {
+        for (;;) {
+            CUDA_TRY(launch_sweep(a, p->dims.data(), nd, p->eval_blocks, p->eval_threads, p->num_sms, st,
+                                  p->profile ? p->stage_ev.data() : nullptr));
+            p->launches += 4 + nd;
+            CUDA_TRY(cudaMemcpyAsync(p->h_ctl, a.ctl, sizeof(WaveCtl), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            if (p->profile) {
+                // classes: [0] eval (per child), [1] control, [2] eval64, [3 + q] hs dim q
+                float t = 0;
+                cudaEventElapsedTime(&t, p->stage_ev[1], p->stage_ev[2]);
+                p->class_ms[0] += t;
+                p->class_launches[0] += 1;
+                cudaEventElapsedTime(&t, p->stage_ev[0], p->stage_ev[1]);
+                p->class_ms[1] += t;
+                cudaEventElapsedTime(&t, p->stage_ev[3 + nd], p->stage_ev[4 + nd]);
+                p->class_ms[1] += t;
+                p->class_launches[1] += 2;
+                cudaEventElapsedTime(&t, p->stage_ev[2], p->stage_ev[3]);
+                p->class_ms[2] += t;
+                p->class_launches[2] += 1;
+                for (int q = 0; q < nd; q++) {
+                    cudaEventElapsedTime(&t, p->stage_ev[3 + q], p->stage_ev[4 + q]);
+                    p->class_ms[3 + q] += t;
+                    p->class_launches[3 + q] += 1;
+                }
+            }
+            if (p->h_ctl->error) { status = IVS_ERR_NOMEM; break; }
+            if (p->h_ctl->top == 0) break;
+            if (p->time_budget_s > 0) {
+                double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                if (el > p->time_budget_s) { status = IVS_ERR_TIMEOUT; break; }
+            }
+        }
+    }
+    CUDA_TRY(cudaEventRecord(p->ev1, st));
+    CUDA_TRY(cudaMemcpyAsync(p->h_stats.data(), a.stats, p->h_stats.size() * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY(cudaEventElapsedTime(&p->last_ms, p->ev0, p->ev1));
+    p->run_status = status;
+    if (status == IVS_ERR_NOMEM) return fail(status, "work queue full: raise workspace or lower wave size");
+    if (status == IVS_ERR_TIMEOUT) return fail(status, "time budget exhausted");
+    return IVS_OK;
+}
+
+static void fill_stats(const ivs_plan *p, int s, ivs_stats *st) {
+    const unsigned long long *v = p->h_stats.data() + (size_t)s * ST_COUNT;
+    st->boxes += (int64_t)v[ST_BOXES];
+    st->excluded_prefilter += (int64_t)v[ST_EXCL_PREFILTER];
+    st->excluded_eval += (int64_t)v[ST_EXCL_EVAL];
+    st->hs_applied += (int64_t)v[ST_HS_APPLIED];
+    st->hs_empty += (int64_t)v[ST_HS_EMPTY];
+    st->hs_contracted += (int64_t)v[ST_HS_CONTRACTED];
+    st->hs_singular += (int64_t)v[ST_HS_SINGULAR];
+    st->accepted += (int64_t)v[ST_ACCEPTED];
+    st->unsplittable += (int64_t)v[ST_UNSPLITTABLE];
+    st->split += (int64_t)v[ST_SPLIT];
+    st->max_depth_seen = std::max(st->max_depth_seen, (int32_t)v[ST_MAX_DEPTH]);
+    st->eval64_boxes += (int64_t)v[ST_EVAL64];
+    st->waves = (int32_t)p->h_ctl->waves;
+    st->device_ms = p->last_ms;
+    st->launches = p->launches;
+}
+
+int ivs_plan_stats(ivs_plan *p, ivs_stats *st) {
+    if (!p || !st) return fail(IVS_ERR_INVALID, "null argument");
+    std::memset(st, 0, sizeof(*st));
+    for (int s = 0; s < p->n_sys; s++) fill_stats(p, s, st);
+    return IVS_OK;
+}
+
+int ivs_plan_result(ivs_plan *p, int32_t s, ivs_result **out) {
+    if (!p || !out || s < 0 || s >= p->n_sys) return fail(IVS_ERR_INVALID, "bad arguments");
+    *out = nullptr;
+    CUDA_TRY(cudaSetDevice(p->device));
+    const int64_t total = std::min<int64_t>(p->h_ctl->out_count, p->out_cap);
+    const int n = p->sys_n[s], nm = p->n_max;
+    std::vector<int32_t> sys(total), flags(total), depth(total);
+    std::vector<double> lo((size_t)total * nm), hi((size_t)total * nm);
+    const DevOut &o = p->args.out;
+    if (total > 0) {
+        CUDA_TRY(cudaMemcpyAsync(sys.data(), o.sys, total * 4, cudaMemcpyDeviceToHost, p->stream));
+        CUDA_TRY(cudaMemcpyAsync(flags.data(), o.flags, total * 4, cudaMemcpyDeviceToHost, p->stream));
+        CUDA_TRY(cudaMemcpyAsync(depth.data(), o.depth, total * 4, cudaMemcpyDeviceToHost, p->stream));
+        for (int j = 0; j < n; j++) {
+            CUDA_TRY(cudaMemcpyAsync(lo.data() + (size_t)j * total, o.lo + (size_t)j * o.cap, total * 8,
+                                     cudaMemcpyDeviceToHost, p->stream));
+            CUDA_TRY(cudaMemcpyAsync(hi.data() + (size_t)j * total, o.hi + (size_t)j * o.cap, total * 8,
+                                     cudaMemcpyDeviceToHost, p->stream));
+        }
+        CUDA_TRY(cudaStreamSynchronize(p->stream));
+    }
+    std::unique_ptr<ivs_result> r(new (std::nothrow) ivs_result());
+    if (!r) return fail(IVS_ERR_NOMEM, "host allocation");
+    r->n = n;
+    std::vector<int64_t> idx;
+    for (int64_t k = 0; k < total; k++)
+        if (sys[k] == s) idx.push_back(k);
+    auto key = [&](int64_t k, int j, bool upper) {
+        double v = (upper ? hi : lo)[(size_t)j * total + k];
+        return v == 0 ? 0.0 : v;
+    };
+    std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
+        for (int j = 0; j < n; j++) {
+            double x = key(a, j, false), y = key(b, j, false);
+            if (x != y) return x < y;
+            x = key(a, j, true);
+            y = key(b, j, true);
+            if (x != y) return x < y;
+        }
+        return false;
+    });
+    r->lo.resize(idx.size() * n);
+    r->hi.resize(idx.size() * n);
+    r->flags.resize(idx.size());
+    r->depth.resize(idx.size());
+    for (size_t q = 0; q < idx.size(); q++) {
+        for (int j = 0; j < n; j++) {
+            r->lo[q * n + j] = key(idx[q], j, false);
+            r->hi[q * n + j] = key(idx[q], j, true);
+        }
+        r->flags[q] = flags[idx[q]];
+        r->depth[q] = depth[idx[q]];
+    }
+    fill_stats(p, s, &r->st);
+    const unsigned long long fl = p->h_stats[(size_t)s * ST_COUNT + ST_FLAGS];
+    int status = p->run_status;
+    if (status == IVS_OK && fl) status = IVS_ERR_BUDGET;
+    r->status = status;
+    *out = r.release();
+    return IVS_OK;
+}
+
+int32_t ivs_plan_kernel_times(ivs_plan *p, ivs_kernel_time *out, int32_t max) {
+    if (!p) return 0;
+    const int32_t total = (int32_t)p->class_ms.size();
+    for (int32_t q = 0; q < total && q < max && out; q++) {
+        std::string name = q == 0 ? "eval" : q == 1 ? "control" : q == 2 ? "eval64" : "hs_n" + std::to_string(p->dims[q - 3]);
+        std::memset(out[q].name, 0, sizeof(out[q].name));
+        std::strncpy(out[q].name, name.c_str(), sizeof(out[q].name) - 1);
+        out[q].launches = p->class_launches[q];
+        out[q].ms = p->class_ms[q];
+    }
+    return total;
+}
+
+int ivs_probe_rate(int32_t kind, int32_t device, double *ops_per_s, double *ms) {
+    if (!ops_per_s || (kind != 0 && kind != 1)) return fail(IVS_ERR_INVALID, "bad arguments");
+    CUDA_TRY(cudaSetDevice(device));
+    int sms = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    double ops = 0;
+    float t = 0;
+    CUDA_TRY(run_probe(kind, sms, &ops, &t));
+    *ops_per_s = ops / (t * 1e-3);
+    if (ms) *ms = t;
+    return IVS_OK;
+}
+
+int64_t ivs_result_count(const ivs_result *r) { return r ? (int64_t)r->flags.size() : 0; }
+int32_t ivs_result_n_vars(const ivs_result *r) { return r ? r->n : 0; }
+int ivs_result_status(const ivs_result *r) { return r ? r->status : IVS_ERR_INVALID; }
+int ivs_result_boxes(const ivs_result *r, double *lo, double *hi, int32_t *flags, int32_t *depth) {
+    if (!r) return fail(IVS_ERR_INVALID, "null result");
+    if (lo && !r->lo.empty()) std::memcpy(lo, r->lo.data(), r->lo.size() * 8);
+    if (hi && !r->hi.empty()) std::memcpy(hi, r->hi.data(), r->hi.size() * 8);
+    if (flags && !r->flags.empty()) std::memcpy(flags, r->flags.data(), r->flags.size() * 4);
+    if (depth && !r->depth.empty()) std::memcpy(depth, r->depth.data(), r->depth.size() * 4);
+    return IVS_OK;
+}
+int ivs_result_stats(const ivs_result *r, ivs_stats *st) {
+    if (!r || !st) return fail(IVS_ERR_INVALID, "null argument");
+    *st = r->st;
+    return IVS_OK;
+}
+void ivs_result_free(ivs_result *r) { delete r; }
+
+int ivs_solve_batch(int32_t n_sys, const ivs_system *systems, const double *const *box_lo,
+                    const double *const *box_hi, const ivs_options *opts, int32_t opts_stride,
+                    ivs_result **outs) {
+    if (!outs) return fail(IVS_ERR_INVALID, "null outs");
+    for (int s = 0; s < n_sys; s++) outs[s] = nullptr;
+    ivs_plan *p = nullptr;
+    int rc = ivs_plan_create(n_sys, systems, box_lo, box_hi, opts, opts_stride, nullptr, &p);
+    if (rc) return rc;
+    int run = ivs_plan_run(p);
+    if (run != IVS_OK && run != IVS_ERR_TIMEOUT && run != IVS_ERR_NOMEM) {
+        ivs_plan_destroy(p);
+        return run;
+    }
+    int first = run;
+    for (int s = 0; s < n_sys; s++) {
+        rc = ivs_plan_result(p, s, &outs[s]);
+        if (rc) {
+            ivs_plan_destroy(p);
+            return rc;
+        }
+        if (first == IVS_OK && outs[s]->status != IVS_OK) first = outs[s]->status;
+    }
+    ivs_plan_destroy(p);
+    return first;
+}
+
+int ivs_solve(const ivs_system *sys, const double *box_lo, const double *box_hi, const ivs_options *opt,
+              ivs_result **out) {
+    if (!out) return fail(IVS_ERR_INVALID, "null out");
+    const double *lo[1] = {box_lo};
+    const double *hi[1] = {box_hi};
+    return ivs_solve_batch(1, sys, lo, hi, opt, 0, out);
+}
+
+}  // extern "C"

@@ -1,0 +1,405 @@
+// ivs_hs.cuh -- Hansen-Sengupta sweep and the accept / split step, one thread per box
+// that survived the evaluation (Section 2.3 eq 14, 17-22; Algorithm 3; Gauss-Jordan of
+// Section 2.4; Algorithm 4 products; Algorithm 1 termination (II); Algorithm 2 split).
+// Templated on the dimension n; the instantiations are spread over several translation
+// units (ivs_hs_*.cu) so that they compile in parallel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ivs_internal.h"
+#include "ivs_interval.cuh"
+#include "ivs_kernels.cuh"
+
+namespace ivs {
+
+namespace hsd {
+constexpr unsigned kFull = 0xFFFFFFFFu;
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
+__device__ __forceinline__ unsigned long long *stat_ptr(const SweepArgs &a, int sys, int slot) {
+    return a.stats + (size_t)sys * ST_COUNT + slot;
+}
+}  // namespace hsd
+using hsd::kFull;
+using hsd::lane_id;
+using hsd::lanemask_lt;
+using hsd::stat_ptr;
+
+// ------------------------------------------------------------------------------------
+// Hansen-Sengupta sweep + accept / split, one thread per surviving box
+// ------------------------------------------------------------------------------------
+
+// per-thread scratch in shared memory, element e of this thread at base[e * T]
+struct Scratch {
+    double *J;     // 2 N N : J (then M) entry (i,j): lo at 2(iN+j), hi at 2(iN+j)+1
+    double *G;     // N N   : Gauss-Jordan working matrix, then B
+    double *X;     // 2 N   : box handed to the polynomial interpreter
+    int *rowid;    // 2 N   : row ids during elimination, then column slots
+    int T;
+};
+
+// interval value of polynomial p over the box in scratch X (runtime variable indices)
+static __device__ __forceinline__ ivd eval_poly_scratch(const DevTables &tb, int p, const double *X, int T) {
+    const int t0 = tb.poly_term_off[p], t1 = tb.poly_term_off[p + 1];
+    ivd acc = {0.0, 0.0};
+    for (int t = t0; t < t1; t++) {
+        const ivd cf = {tb.term_clo[t], tb.term_chi[t]};
+        const int f0 = tb.term_fac_off[t], f1 = tb.term_fac_off[t + 1];
+        ivd v;
+        if (f0 == f1) {
+            v = cf;
+        } else {
+            unsigned fc = tb.fac[f0];
+            unsigned j = fc >> 4;
+            ivd prod = iv_pow(ivd{X[(2 * j) * T], X[(2 * j + 1) * T]}, (int)(fc & 15u));
+            for (int f = f0 + 1; f < f1; f++) {
+                fc = tb.fac[f];
+                j = fc >> 4;
+                prod = iv_mul(prod, iv_pow(ivd{X[(2 * j) * T], X[(2 * j + 1) * T]}, (int)(fc & 15u)));
+            }
+            v = iv_mul(cf, prod);
+        }
+        acc = (t == t0) ? v : iv_add(acc, v);
+    }
+    return acc;
+}
+
+static __device__ __forceinline__ double midpoint_rn(double lo, double hi) {
+    return __dmul_rn(0.5, __dadd_rn(lo, hi));
+}
+
+// One Gauss-Seidel sweep on B f(x) + B J(X)(z - x) = 0 (eq 14, 21, 22).
+// Returns 0 (Xo written), 1 (empty), 2 (skipped: singular preconditioner).
+template <int N>
+__device__ int hs_sweep(const DevTables &tb, const DevSys &S, const double *Xlo, const double *Xhi,
+                        double *Xolo, double *Xohi, const Scratch &sc) {
+    const int T = sc.T;
+    double *X = sc.X;
+    double *J = sc.J;
+    double *G = sc.G;
+    int *rowid = sc.rowid;
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        X[(2 * j) * T] = Xlo[j];
+        X[(2 * j + 1) * T] = Xhi[j];
+    }
+    // J(X): derivative polynomials compiled on the host
+    for (int q = 0; q < N * N; q++) {
+        const ivd v = eval_poly_scratch(tb, S.j_poly + q, X, T);
+        J[(2 * q) * T] = v.lo;
+        J[(2 * q + 1) * T] = v.hi;
+    }
+    // A = mid(J(X)) (round to nearest)
+    bool bad = false;
+    for (int q = 0; q < N * N; q++) {
+        const double m = midpoint_rn(J[(2 * q) * T], J[(2 * q + 1) * T]);
+        bad |= !isfinite(m);
+        G[q * T] = m;
+    }
+    if (bad) return 2;
+    // Gauss-Jordan with partial pivoting (Section 2.4), in place: after step k, storage
+    // column k holds column rowid[k] of the right half [.|I] (the classic in-place form;
+    // entries of untouched identity columns are 0 and their updates are exact no-ops).
+#pragma unroll
+    for (int k = 0; k < N; k++) rowid[k * T] = k;
+    for (int k = 0; k < N; k++) {
+        int piv = k;
+        double best = fabs(G[(k * N + k) * T]);
+        for (int i = k + 1; i < N; i++) {
+            const double v = fabs(G[(i * N + k) * T]);
+            if (v > best) { best = v; piv = i; }
+        }
+        if (!(best > 0.0) || !isfinite(best)) return 2;
+        if (piv != k) {
+            for (int j = 0; j < N; j++) {
+                const double t = G[(k * N + j) * T];
+                G[(k * N + j) * T] = G[(piv * N + j) * T];
+                G[(piv * N + j) * T] = t;
+            }
+            const int t = rowid[k * T];
+            rowid[k * T] = rowid[piv * T];
+            rowid[piv * T] = t;
+        }
+        const double pv = G[(k * N + k) * T];
+        const double rp = __ddiv_rn(1.0, pv);       // eq 23 on the identity column
+        for (int j = 0; j < N; j++)
+            if (j != k) G[(k * N + j) * T] = __ddiv_rn(G[(k * N + j) * T], pv);   // eq 23
+        G[(k * N + k) * T] = rp;
+        for (int i = 0; i < N; i++) {                                          // eq 24
+            if (i == k) continue;
+            const double f = G[(i * N + k) * T];
+            for (int j = 0; j < N; j++)
+                if (j != k) G[(i * N + j) * T] = __dsub_rn(G[(i * N + j) * T], __dmul_rn(f, G[(k * N + j) * T]));
+            G[(i * N + k) * T] = __dsub_rn(0.0, __dmul_rn(f, rp));
+        }
+    }
+    // storage column k is column rowid[k] of B: slot_of[u] = k with rowid[k] = u
+    int *slot_of = rowid + N * T;
+    for (int k = 0; k < N; k++) slot_of[rowid[k * T] * T] = k;
+    for (int i = 0; i < N; i++) {
+        double rowv[N];
+#pragma unroll
+        for (int u = 0; u < N; u++) rowv[u] = G[(i * N + slot_of[u * T]) * T];
+#pragma unroll
+        for (int u = 0; u < N; u++) {
+            if (!isfinite(rowv[u])) bad = true;
+            G[(i * N + u) * T] = rowv[u];
+        }
+    }
+    if (bad) return 2;
+    // x = mid(X); f(x) as a thin-box evaluation
+    double xc[N];
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        xc[j] = midpoint_rn(Xlo[j], Xhi[j]);
+        X[(2 * j) * T] = xc[j];
+        X[(2 * j + 1) * T] = xc[j];
+    }
+    ivd fx[N];
+#pragma unroll
+    for (int i = 0; i < N; i++) fx[i] = eval_poly_scratch(tb, S.f_poly + i, X, T);
+    // M = B J(X) in place of J (column by column), r = B f(x) (Algorithm 4, outward)
+    for (int j = 0; j < N; j++) {
+        ivd col[N];
+#pragma unroll
+        for (int u = 0; u < N; u++) col[u] = ivd{J[(2 * (u * N + j)) * T], J[(2 * (u * N + j) + 1) * T]};
+        for (int i = 0; i < N; i++) {
+            ivd acc = iv_smul(G[(i * N) * T], col[0]);
+#pragma unroll
+            for (int u = 1; u < N; u++) acc = iv_add(acc, iv_smul(G[(i * N + u) * T], col[u]));
+            J[(2 * (i * N + j)) * T] = acc.lo;
+            J[(2 * (i * N + j) + 1) * T] = acc.hi;
+        }
+    }
+    ivd r[N];
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        ivd acc = iv_smul(G[(i * N) * T], fx[0]);
+#pragma unroll
+        for (int u = 1; u < N; u++) acc = iv_add(acc, iv_smul(G[(i * N + u) * T], fx[u]));
+        r[i] = acc;
+    }
+    // Gauss-Seidel (eq 21-22)
+#pragma unroll
+    for (int j = 0; j < N; j++) { Xolo[j] = Xlo[j]; Xohi[j] = Xhi[j]; }
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        ivd s = r[i];
+#pragma unroll
+        for (int j = 0; j < N; j++) {
+            if (j == i) continue;
+            const ivd mij = {J[(2 * (i * N + j)) * T], J[(2 * (i * N + j) + 1) * T]};
+            const ivd d = iv_sub(ivd{Xolo[j], Xohi[j]}, ivd{xc[j], xc[j]});
+            s = iv_add(s, iv_mul(mij, d));
+        }
+        const ivd D = {J[(2 * (i * N + i)) * T], J[(2 * (i * N + i) + 1) * T]};
+        if (isnan(s.lo) || isnan(s.hi) || isnan(D.lo) || isnan(D.hi)) continue;
+        ivd pc[2];
+        const int np = iv_extdiv(s, D, pc);
+        double lo = 0.0, hi = 0.0;
+        bool any = false;
+        for (int q = 0; q < np; q++) {
+            const ivd Y = iv_sub(ivd{xc[i], xc[i]}, pc[q]);
+            const double a0 = d_max(Xlo[i], Y.lo), b0 = d_min(Xhi[i], Y.hi);
+            if (d_key(a0) <= d_key(b0) || a0 == b0) {
+                lo = any ? d_min(lo, a0) : a0;
+                hi = any ? d_max(hi, b0) : b0;
+                any = true;
+            }
+        }
+        if (!any) return 1;
+        Xolo[i] = lo;
+        Xohi[i] = hi;
+    }
+    return 0;
+}
+
+template <int N>
+__global__ void __launch_bounds__(64) k_hs(SweepArgs a) {
+    extern __shared__ double smem[];
+    const int T = blockDim.x, tid = threadIdx.x;
+    Scratch sc;
+    sc.T = T;
+    sc.J = smem + tid;
+    sc.G = smem + (size_t)2 * N * N * T + tid;
+    sc.X = smem + (size_t)3 * N * N * T + tid;
+    sc.rowid = reinterpret_cast<int *>(smem + (size_t)(3 * N * N + 2 * N) * T) + tid;
+
+    WaveCtl *ctl = a.ctl;
+    const int64_t count = ctl->surv_count[N];
+    const Surv *list = a.surv + (size_t)N * a.surv_cap;
+    const unsigned lane = lane_id();
+    for (;;) {
+        // each warp takes the next 32 boxes, so every SM gets a share of a small sweep
+        unsigned long long ws = 0;
+        if (lane == 0) ws = atomicAdd((unsigned long long *)&ctl->hs_cursor[N], 32ull);
+        ws = __shfl_sync(kFull, ws, 0);
+        if ((long long)ws >= count) break;
+        const int64_t idx = (int64_t)ws + lane;
+        const bool active = idx < count;
+        int fate = 0;   // 0 none/dropped, 1 accepted, 2 new parent
+        int flag = 0, sys = 0, depth = 0;
+        double Xlo[N], Xhi[N], xm[N];
+        unsigned st_app = 0, st_empty = 0, st_con = 0, st_sing = 0, st_uns = 0;
+        if (active) {
+            const Surv sv = list[idx];
+            const int64_t pi = sv.parent;
+            sys = a.q.sys[pi];
+            const uint32_t meta = a.q.meta[pi];
+            const bool root = (meta & kRootFlag) != 0;
+            depth = (int)(meta & kDepthMask) + (root ? 0 : 1);
+            const DevSys S = a.tb.sys[sys];
+#pragma unroll
+            for (int j = 0; j < N; j++) {
+                const bool up = (sv.child >> j) & 1u;
+                Xlo[j] = up ? a.q.mid[j * a.q.cap + pi] : a.q.lo[j * a.q.cap + pi];
+                Xhi[j] = up ? a.q.hi[j * a.q.cap + pi] : a.q.mid[j * a.q.cap + pi];
+            }
+            bool dropped = false;
+            if (S.hs_enable && depth >= S.hs_min_depth) {
+                const int iters = S.hs_iters > 0 ? S.hs_iters : 1;
+                for (int it = 0; it < iters; it++) {
+                    st_app++;
+                    double Ylo[N], Yhi[N];
+                    const int rc = hs_sweep<N>(a.tb, S, Xlo, Xhi, Ylo, Yhi, sc);
+                    if (rc == 1) { dropped = true; break; }
+                    if (rc == 2) { st_sing++; break; }
+                    bool changed = false;
+#pragma unroll
+                    for (int j = 0; j < N; j++) {
+                        changed |= (Ylo[j] != Xlo[j]) || (Yhi[j] != Xhi[j]);
+                        Xlo[j] = Ylo[j];
+                        Xhi[j] = Yhi[j];
+                    }
+                    st_con += changed ? 1u : 0u;
+                }
+            }
+            if (dropped) {
+                st_empty++;
+            } else {
+                // Algorithm 1 termination (II): width test; otherwise split at midpoints
+                double w = 0.0;
+                int jw = 0;
+#pragma unroll
+                for (int j = 0; j < N; j++) {
+                    const double wj = __dsub_rn(Xhi[j], Xlo[j]);
+                    if (d_key(wj) > d_key(w)) { w = wj; jw = j; }
+                }
+                if (d_key(w) <= d_key(S.tol)) {
+                    fate = 1;
+                    flag = 1;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < N; j++) xm[j] = midpoint_rn(Xlo[j], Xhi[j]);
+                    double mw = xm[0], lw = Xlo[0], hw = Xhi[0];
+#pragma unroll
+                    for (int j = 1; j < N; j++)
+                        if (j == jw) { mw = xm[j]; lw = Xlo[j]; hw = Xhi[j]; }
+                    if (mw == lw || mw == hw) {
+                        fate = 1;
+                        flag = 2;
+                        st_uns++;
+                    } else if (depth + 1 > S.max_depth) {
+                        fate = 1;
+                        flag = 4;
+                    } else {
+                        fate = 2;
+                    }
+                }
+            }
+        }
+        // accepted boxes
+        const unsigned ma = __ballot_sync(kFull, fate == 1);
+        if (ma) {
+            unsigned long long pos = 0;
+            if (lane == 0) pos = atomicAdd((unsigned long long *)&ctl->out_count, (unsigned long long)__popc(ma));
+            pos = __shfl_sync(kFull, pos, 0);
+            if (fate == 1) {
+                const long long k = (long long)(pos + __popc(ma & lanemask_lt()));
+                if (k < a.out.cap) {
+#pragma unroll
+                    for (int j = 0; j < N; j++) {
+                        a.out.lo[j * a.out.cap + k] = Xlo[j];
+                        a.out.hi[j * a.out.cap + k] = Xhi[j];
+                    }
+                    a.out.sys[k] = sys;
+                    a.out.flags[k] = flag;
+                    a.out.depth[k] = depth;
+                } else {
+                    atomicOr(stat_ptr(a, sys, ST_FLAGS), (unsigned long long)kFlagResultOverflow);
+                }
+                if (flag == 4) atomicOr(stat_ptr(a, sys, ST_FLAGS), (unsigned long long)kFlagDepthCut);
+            }
+        }
+        // new parents
+        const unsigned ms = __ballot_sync(kFull, fate == 2);
+        if (ms) {
+            unsigned long long pos = 0;
+            if (lane == 0) pos = atomicAdd((unsigned long long *)&ctl->staged, (unsigned long long)__popc(ms));
+            pos = __shfl_sync(kFull, pos, 0);
+            if (fate == 2) {
+                const long long k = (long long)(pos + __popc(ms & lanemask_lt()));
+                if (k < a.stage.cap) {
+#pragma unroll
+                    for (int j = 0; j < N; j++) {
+                        a.stage.lo[j * a.stage.cap + k] = Xlo[j];
+                        a.stage.mid[j * a.stage.cap + k] = xm[j];
+                        a.stage.hi[j * a.stage.cap + k] = Xhi[j];
+                    }
+                    a.stage.sys[k] = sys;
+                    a.stage.meta[k] = (uint32_t)depth & kDepthMask;
+                } else {
+                    ctl->error = 1;
+                }
+            }
+        }
+        // statistics: one atomic per warp when the warp holds a single system
+        const int sys0 = __shfl_sync(kFull, sys, 0);
+        const bool uniform = __all_sync(kFull, !active || sys == sys0);
+        unsigned v[7] = {st_app, st_empty, st_con, st_sing, (fate == 1 && flag != 4) ? 1u : 0u, st_uns,
+                         fate == 2 ? 1u : 0u};
+        const int slot[7] = {ST_HS_APPLIED, ST_HS_EMPTY, ST_HS_CONTRACTED, ST_HS_SINGULAR, ST_ACCEPTED,
+                             ST_UNSPLITTABLE, ST_SPLIT};
+        if (uniform) {
+#pragma unroll
+            for (int q = 0; q < 7; q++) {
+                const unsigned tot = __reduce_add_sync(kFull, v[q]);
+                if (lane == 0 && tot) atomicAdd(stat_ptr(a, sys0, slot[q]), (unsigned long long)tot);
+            }
+        } else if (active) {
+#pragma unroll
+            for (int q = 0; q < 7; q++)
+                if (v[q]) atomicAdd(stat_ptr(a, sys, slot[q]), (unsigned long long)v[q]);
+        }
+    }
+}
+
+// ---- launcher -------------------------------------------------------------------
+
+inline size_t hs_smem_for_(int n, int threads) {
+    return (size_t)threads * ((size_t)(3 * n * n + 2 * n) * sizeof(double) + (size_t)2 * n * sizeof(int));
+}
+
+inline int hs_threads_for_(int n) {
+    // small blocks (1-2 warps) spread a sweep's few boxes over all SMs
+    return hs_smem_for_(n, 64) <= 110 * 1024 ? 64 : 32;
+}
+
+template <int N>
+static cudaError_t launch_hs_n(const SweepArgs &a, int num_sms, cudaStream_t st) {
+    static int per_sm = 0;   // blocks per SM, found once per process (one device)
+    const int T = hs_threads_for_(N);
+    const size_t smem = hs_smem_for_(N, T);
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_hs<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hs<N>, T, smem);
+        if (e != cudaSuccess) return e;
+        per_sm = b < 1 ? 1 : b;
+    }
+    k_hs<N><<<num_sms * per_sm, T, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ivs

@@ -1,0 +1,101 @@
+// ivs_internal.h -- layouts shared by the host runtime and the kernels of the library.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+namespace ivs {
+
+constexpr int kMaxVars = 16;
+constexpr int kMaxExp = 15;
+
+// Parent-entry meta word: depth in the low 16 bits, ROOT flag (the entry is an initial
+// box that is evaluated itself, fan-out 1, not split first).
+constexpr uint32_t kRootFlag = 1u << 30;
+constexpr uint32_t kDepthMask = 0xFFFFu;
+
+// per-system statistics slots (int64 counters on the device)
+enum Stat : int {
+    ST_BOXES = 0,
+    ST_EXCL_PREFILTER,
+    ST_EXCL_EVAL,
+    ST_HS_APPLIED,
+    ST_HS_EMPTY,
+    ST_HS_CONTRACTED,
+    ST_HS_SINGULAR,
+    ST_ACCEPTED,
+    ST_UNSPLITTABLE,
+    ST_SPLIT,
+    ST_MAX_DEPTH,
+    ST_FLAGS,          // bit 0: results overflowed, bit 1: depth cut, bit 2: box budget hit
+    ST_EVAL64,         // boxes that ran the FP64 evaluation
+    ST_COUNT
+};
+constexpr int64_t kFlagResultOverflow = 1, kFlagDepthCut = 2, kFlagBudget = 4;
+
+// Compiled system, resident on the device.  Polynomials (F_i, then J_ij row-major) index
+// a shared term table; each term is a coefficient interval and a list of factors
+// (var << 4 | exponent), exponents >= 1.
+struct DevSys {
+    int32_t n, m;
+    int32_t f_poly;        // first polynomial of F (m of them)
+    int32_t j_poly;        // first polynomial of J (m * n of them), -1 if none
+    double tol;
+    int32_t hs_enable, hs_min_depth, hs_iters, max_depth;
+    int32_t prefilter;
+    int32_t pad;
+    int64_t max_boxes;
+};
+
+struct DevTables {
+    const DevSys *sys;
+    const int32_t *poly_term_off;   // [n_polys + 1]
+    const double *term_clo;          // [n_terms]
+    const double *term_chi;
+    const float *term_clo32;         // outward float copies of the coefficients
+    const float *term_chi32;
+    const int32_t *term_fac_off;     // [n_terms + 1]
+    const uint8_t *fac;              // [n_factors]
+};
+
+// Queue of parent boxes (boxes to split), structure of arrays with capacity `cap`:
+// coordinate j of entry i at lo[j * cap + i] (likewise mid, hi).
+struct DevQueue {
+    double *lo, *mid, *hi;
+    int32_t *sys;
+    uint32_t *meta;
+    int64_t cap;
+};
+
+// Accepted boxes (output list).
+struct DevOut {
+    double *lo, *hi;
+    int32_t *sys;
+    int32_t *flags;
+    int32_t *depth;
+    int64_t cap;
+};
+
+// Control block of the sweep loop (device memory).
+struct WaveCtl {
+    int64_t top;            // queue size
+    int64_t base;           // first parent popped by this sweep
+    int64_t k;              // parents popped by this sweep
+    int64_t staged;         // new parents written to the staging queue
+    int64_t out_count;      // accepted boxes written
+    int32_t cursor;         // evaluation kernel's parent cursor
+    int32_t error;          // sticky: 1 = queue full
+    int64_t surv_count[kMaxVars + 1];   // survivors per n (index n)
+    int64_t hs_cursor[kMaxVars + 1];    // Hansen-Sengupta kernels' work cursors
+    int64_t cand_count;                 // FP32 survivors waiting for the FP64 evaluation
+    int64_t cand_cursor;
+    int64_t waves;
+    int64_t wave_limit;     // the device loop stops when waves reaches it
+};
+
+// survivor of the evaluation: parent index in the queue, child index
+struct Surv {
+    uint32_t parent;
+    uint32_t child;
+};
+
+}  // namespace ivs

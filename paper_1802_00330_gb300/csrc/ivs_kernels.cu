@@ -1,0 +1,464 @@
+// ivs_kernels.cu -- the per-box sweep over the device queue (sm_103a).
+//
+// Paper map: Definition 1-2 and Algorithm 2 (evaluation + exclusion of the 2^n children
+// of each parent), Section 2.3 / Algorithm 3 (Hansen-Sengupta sweep: Jacobian, Gauss-Jordan
+// preconditioner of Section 2.4, Algorithm 4 products, Gauss-Seidel of eq 21-22 with the
+// extended division of eq 10), Algorithm 1 (accept at the desired width or split again).
+// Every operation sequence matches the serial definition step for step (same fold orders,
+// same roundings), so the sorted result set is identical to the serial solver's.
+#include <cuda_runtime.h>
+
+#include "ivs_internal.h"
+#include "ivs_interval.cuh"
+#include "ivs_kernels.cuh"
+
+namespace ivs {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kEvalMaxThreads = 256;
+constexpr int kEvalMaxWarps = kEvalMaxThreads / 32;
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
+
+__device__ __forceinline__ unsigned long long *stat_ptr(const SweepArgs &a, int sys, int slot) {
+    return a.stats + (size_t)sys * ST_COUNT + slot;
+}
+
+// ------------------------------------------------------------------------------------
+// sweep control
+// ------------------------------------------------------------------------------------
+
+// Pops K parents from the top: the worst case (every child kept and split again) must
+// fit both the staging queue (wave_children entries) and the queue itself.
+__global__ void k_wave_begin(SweepArgs a) {
+    if (threadIdx.x != 0) return;
+    WaveCtl *c = a.ctl;
+    int64_t top = c->top;
+    int64_t fan = (int64_t)1 << a.max_fan_shift;
+    int64_t k = a.wave_children / fan;
+    if (k > top) k = top;
+    if (fan > 1) {
+        int64_t room = (a.q.cap - top) / (fan - 1);
+        if (k > room) k = room;
+    }
+    if (k <= 0 && top > 0) { c->error = 1; k = 0; }
+    c->base = top - k;
+    c->k = k;
+    c->cursor = 0;
+    c->staged = 0;
+    for (int n = 0; n <= kMaxVars; n++) { c->surv_count[n] = 0; c->hs_cursor[n] = 0; }
+    c->cand_count = 0;
+    c->cand_cursor = 0;
+    c->waves += 1;
+}
+
+__global__ void k_commit(SweepArgs a, int n_max) {
+    const WaveCtl *c = a.ctl;
+    const int64_t staged = c->staged, base = c->base;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < staged; i += stride) {
+        const int64_t d = base + i;
+        for (int j = 0; j < n_max; j++) {
+            a.q.lo[j * a.q.cap + d] = a.stage.lo[j * a.stage.cap + i];
+            a.q.mid[j * a.q.cap + d] = a.stage.mid[j * a.stage.cap + i];
+            a.q.hi[j * a.q.cap + d] = a.stage.hi[j * a.stage.cap + i];
+        }
+        a.q.sys[d] = a.stage.sys[i];
+        a.q.meta[d] = a.stage.meta[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->top = base + staged;
+}
+
+__global__ void k_seed_roots(SweepArgs a, const double *box_lo, const double *box_hi,
+                             const int32_t *root_depth, int n_sys, int n_max) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sys; s += gridDim.x * blockDim.x) {
+        for (int j = 0; j < n_max; j++) {
+            a.q.lo[j * a.q.cap + s] = box_lo[(size_t)s * n_max + j];
+            a.q.mid[j * a.q.cap + s] = box_hi[(size_t)s * n_max + j];   // a root's only
+            a.q.hi[j * a.q.cap + s] = box_hi[(size_t)s * n_max + j];    // child is itself
+        }
+        a.q.sys[s] = s;
+        a.q.meta[s] = kRootFlag | ((uint32_t)root_depth[s] & kDepthMask);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        WaveCtl *c = a.ctl;
+        c->top = n_sys;
+        c->base = 0;
+        c->k = 0;
+        c->staged = 0;
+        c->out_count = 0;
+        c->cursor = 0;
+        c->error = 0;
+        c->waves = 0;
+        c->cand_count = 0;
+        c->cand_cursor = 0;
+        c->wave_limit = 0x7FFFFFFFFFFFFFFFLL;
+        for (int n = 0; n <= kMaxVars; n++) { c->surv_count[n] = 0; c->hs_cursor[n] = 0; }
+    }
+}
+
+__global__ void k_loop_cond(SweepArgs a, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0) return;
+    const WaveCtl *c = a.ctl;
+    const bool more = c->top > 0 && c->error == 0 && c->waves < c->wave_limit;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// ------------------------------------------------------------------------------------
+// evaluation: natural interval extension of every equation on each child box
+// ------------------------------------------------------------------------------------
+
+// FP64 F_i over child c of the warp's parent.  Coordinates: s_p[0][j] = lo_j,
+// s_p[1][j] = mid_j, s_p[2][j] = hi_j; child c has [lo, mid] or [mid, hi] in coordinate
+// j by bit j of c.  Returns false as soon as one F_i excludes 0.
+__device__ bool eval_keep64(const DevTables &tb, const DevSys &S, const double (*s_p)[kMaxVars],
+                            unsigned c) {
+    for (int i = 0; i < S.m; i++) {
+        const int p = S.f_poly + i;
+        const int t0 = tb.poly_term_off[p], t1 = tb.poly_term_off[p + 1];
+        ivd acc = {0.0, 0.0};
+        for (int t = t0; t < t1; t++) {
+            const ivd cf = {tb.term_clo[t], tb.term_chi[t]};
+            const int f0 = tb.term_fac_off[t], f1 = tb.term_fac_off[t + 1];
+            ivd v;
+            if (f0 == f1) {
+                v = cf;
+            } else {
+                unsigned fc = tb.fac[f0];
+                unsigned j = fc >> 4, up = (c >> j) & 1u;
+                ivd prod = iv_pow(ivd{s_p[up][j], s_p[up + 1][j]}, (int)(fc & 15u));
+                for (int f = f0 + 1; f < f1; f++) {
+                    fc = tb.fac[f];
+                    j = fc >> 4;
+                    up = (c >> j) & 1u;
+                    prod = iv_mul(prod, iv_pow(ivd{s_p[up][j], s_p[up + 1][j]}, (int)(fc & 15u)));
+                }
+                v = iv_mul(cf, prod);
+            }
+            acc = (t == t0) ? v : iv_add(acc, v);
+        }
+        if (d_pos(acc.lo) || d_neg(acc.hi)) return false;
+    }
+    return true;
+}
+
+// FP32 outward evaluation of the same operation sequence.  s_f[0][j] = rd32(lo_j),
+// s_f[1][j] = rd32(mid_j), s_f[2][j] = ru32(mid_j), s_f[3][j] = ru32(hi_j).
+__device__ bool eval_keep32(const DevTables &tb, const DevSys &S, const float (*s_f)[kMaxVars],
+                            unsigned c) {
+    for (int i = 0; i < S.m; i++) {
+        const int p = S.f_poly + i;
+        const int t0 = tb.poly_term_off[p], t1 = tb.poly_term_off[p + 1];
+        ivf acc = {0.0f, 0.0f};
+        for (int t = t0; t < t1; t++) {
+            const ivf cf = {tb.term_clo32[t], tb.term_chi32[t]};
+            const int f0 = tb.term_fac_off[t], f1 = tb.term_fac_off[t + 1];
+            ivf v;
+            if (f0 == f1) {
+                v = cf;
+            } else {
+                unsigned fc = tb.fac[f0];
+                unsigned j = fc >> 4, up = (c >> j) & 1u;
+                ivf prod = fv_pow(ivf{s_f[up][j], s_f[up + 2][j]}, (int)(fc & 15u));
+                for (int f = f0 + 1; f < f1; f++) {
+                    fc = tb.fac[f];
+                    j = fc >> 4;
+                    up = (c >> j) & 1u;
+                    prod = fv_mul(prod, fv_pow(ivf{s_f[up][j], s_f[up + 2][j]}, (int)(fc & 15u)));
+                }
+                v = fv_mul(cf, prod);
+            }
+            acc = (t == t0) ? v : fv_add(acc, v);
+        }
+        if (acc.lo > 0.0f || acc.hi < 0.0f) return false;
+    }
+    return true;
+}
+
+// One warp per parent (taken from a shared cursor), one lane per child.
+__global__ void __launch_bounds__(kEvalMaxThreads) k_eval(SweepArgs a) {
+    __shared__ double s_p[kEvalMaxWarps][3][kMaxVars];
+    __shared__ float s_f[kEvalMaxWarps][4][kMaxVars];
+    const unsigned lane = lane_id();
+    const int w = threadIdx.x >> 5;
+    WaveCtl *ctl = a.ctl;
+    const int64_t base = ctl->base, K = ctl->k;
+    for (;;) {
+        int p = 0;
+        if (lane == 0) p = atomicAdd(&ctl->cursor, 1);
+        p = __shfl_sync(kFull, p, 0);
+        if (p >= K) break;
+        const int64_t pi = base + p;
+        const int sys = a.q.sys[pi];
+        const uint32_t meta = a.q.meta[pi];
+        const DevSys S = a.tb.sys[sys];
+        const bool root = (meta & kRootFlag) != 0;
+        const int depth = (int)(meta & kDepthMask) + (root ? 0 : 1);
+        if (S.max_boxes > 0) {
+            unsigned long long done = *(volatile unsigned long long *)stat_ptr(a, sys, ST_BOXES);
+            if ((long long)done >= S.max_boxes) {
+                if (lane == 0) atomicOr(stat_ptr(a, sys, ST_FLAGS), (unsigned long long)kFlagBudget);
+                continue;
+            }
+        }
+        const int n = S.n;
+        if ((int)lane < n) {
+            const double lo = a.q.lo[lane * a.q.cap + pi];
+            const double mid = a.q.mid[lane * a.q.cap + pi];
+            const double hi = a.q.hi[lane * a.q.cap + pi];
+            s_p[w][0][lane] = lo;
+            s_p[w][1][lane] = mid;
+            s_p[w][2][lane] = hi;
+            s_f[w][0][lane] = __double2float_rd(lo);
+            s_f[w][1][lane] = __double2float_rd(mid);
+            s_f[w][2][lane] = __double2float_ru(mid);
+            s_f[w][3][lane] = __double2float_ru(hi);
+        }
+        __syncwarp();
+        const unsigned fan = root ? 1u : (1u << n);
+        unsigned cnt_pre = 0, cnt_ev = 0, cnt_64 = 0;
+        for (unsigned c0 = 0; c0 < fan; c0 += 32) {
+            const unsigned c = c0 + lane;
+            const bool active = c < fan;
+            bool keep = false, cand = false;
+            if (active) {
+                if (S.prefilter) {
+                    // FP32 stage; its survivors are evaluated in FP64 densely by k_eval64
+                    cand = eval_keep32(a.tb, S, s_f[w], c);
+                    cnt_pre += cand ? 0u : 1u;
+                } else {
+                    cnt_64 += 1;
+                    keep = eval_keep64(a.tb, S, s_p[w], c);
+                    cnt_ev += keep ? 0u : 1u;
+                }
+            }
+            const unsigned km = __ballot_sync(kFull, keep);
+            if (km) {
+                unsigned long long pos = 0;
+                if (lane == 0) pos = atomicAdd((unsigned long long *)&ctl->surv_count[n], (unsigned long long)__popc(km));
+                pos = __shfl_sync(kFull, pos, 0);
+                if (keep) {
+                    const unsigned long long k = pos + __popc(km & lanemask_lt());
+                    if ((long long)k < a.surv_cap) a.surv[(size_t)n * a.surv_cap + k] = Surv{(uint32_t)pi, c};
+                    else ctl->error = 1;
+                }
+            }
+            const unsigned cm = __ballot_sync(kFull, cand);
+            if (cm) {
+                unsigned long long pos = 0;
+                if (lane == 0) pos = atomicAdd((unsigned long long *)&ctl->cand_count, (unsigned long long)__popc(cm));
+                pos = __shfl_sync(kFull, pos, 0);
+                if (cand) {
+                    const unsigned long long k = pos + __popc(cm & lanemask_lt());
+                    if ((long long)k < a.surv_cap) a.cand[k] = Surv{(uint32_t)pi, c};
+                    else ctl->error = 1;
+                }
+            }
+        }
+        cnt_pre = __reduce_add_sync(kFull, cnt_pre);
+        cnt_ev = __reduce_add_sync(kFull, cnt_ev);
+        cnt_64 = __reduce_add_sync(kFull, cnt_64);
+        if (lane == 0) {
+            atomicAdd(stat_ptr(a, sys, ST_BOXES), (unsigned long long)fan);
+            if (cnt_pre) atomicAdd(stat_ptr(a, sys, ST_EXCL_PREFILTER), (unsigned long long)cnt_pre);
+            if (cnt_ev) atomicAdd(stat_ptr(a, sys, ST_EXCL_EVAL), (unsigned long long)cnt_ev);
+            if (cnt_64) atomicAdd(stat_ptr(a, sys, ST_EVAL64), (unsigned long long)cnt_64);
+            atomicMax(stat_ptr(a, sys, ST_MAX_DEPTH), (unsigned long long)depth);
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// FP64 evaluation of the FP32 survivors, one thread per candidate (dense)
+// ------------------------------------------------------------------------------------
+
+constexpr int kEval64Threads = 128;
+
+// F_i over a box held in per-thread shared memory (runtime variable indices)
+__device__ bool eval_keep64_box(const DevTables &tb, const DevSys &S, const double *X, int T) {
+    for (int i = 0; i < S.m; i++) {
+        const int p = S.f_poly + i;
+        const int t0 = tb.poly_term_off[p], t1 = tb.poly_term_off[p + 1];
+        ivd acc = {0.0, 0.0};
+        for (int t = t0; t < t1; t++) {
+            const ivd cf = {tb.term_clo[t], tb.term_chi[t]};
+            const int f0 = tb.term_fac_off[t], f1 = tb.term_fac_off[t + 1];
+            ivd v;
+            if (f0 == f1) {
+                v = cf;
+            } else {
+                unsigned fc = tb.fac[f0];
+                unsigned j = fc >> 4;
+                ivd prod = iv_pow(ivd{X[(2 * j) * T], X[(2 * j + 1) * T]}, (int)(fc & 15u));
+                for (int f = f0 + 1; f < f1; f++) {
+                    fc = tb.fac[f];
+                    j = fc >> 4;
+                    prod = iv_mul(prod, iv_pow(ivd{X[(2 * j) * T], X[(2 * j + 1) * T]}, (int)(fc & 15u)));
+                }
+                v = iv_mul(cf, prod);
+            }
+            acc = (t == t0) ? v : iv_add(acc, v);
+        }
+        if (d_pos(acc.lo) || d_neg(acc.hi)) return false;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kEval64Threads) k_eval64(SweepArgs a) {
+    __shared__ double sX[2 * kMaxVars * kEval64Threads];
+    const int T = blockDim.x, tid = threadIdx.x;
+    double *X = sX + tid;
+    WaveCtl *ctl = a.ctl;
+    const int64_t count = ctl->cand_count;
+    const unsigned lane = lane_id();
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd((unsigned long long *)&ctl->cand_cursor, 32ull);
+        base = __shfl_sync(kFull, base, 0);
+        if ((long long)base >= count) break;
+        const int64_t idx = (int64_t)base + lane;
+        const bool active = idx < count;
+        bool keep = false;
+        int sys = 0, n = 0;
+        Surv sv{0, 0};
+        if (active) {
+            sv = a.cand[idx];
+            const int64_t pi = sv.parent;
+            sys = a.q.sys[pi];
+            const DevSys S = a.tb.sys[sys];
+            n = S.n;
+            for (int j = 0; j < n; j++) {
+                const bool up = (sv.child >> j) & 1u;
+                X[(2 * j) * T] = up ? a.q.mid[j * a.q.cap + pi] : a.q.lo[j * a.q.cap + pi];
+                X[(2 * j + 1) * T] = up ? a.q.hi[j * a.q.cap + pi] : a.q.mid[j * a.q.cap + pi];
+            }
+            keep = eval_keep64_box(a.tb, S, X, T);
+        }
+        // survivors into the list of their dimension; counters per system
+        const int sys0 = __shfl_sync(kFull, sys, 0);
+        const int n0 = __shfl_sync(kFull, n, 0);
+        const bool uniform = __all_sync(kFull, !active || (sys == sys0 && n == n0));
+        if (uniform) {
+            const unsigned km = __ballot_sync(kFull, keep);
+            if (km) {
+                unsigned long long pos = 0;
+                if (lane == 0) pos = atomicAdd((unsigned long long *)&ctl->surv_count[n0], (unsigned long long)__popc(km));
+                pos = __shfl_sync(kFull, pos, 0);
+                if (keep) {
+                    const unsigned long long k = pos + __popc(km & lanemask_lt());
+                    if ((long long)k < a.surv_cap) a.surv[(size_t)n0 * a.surv_cap + k] = sv;
+                    else ctl->error = 1;
+                }
+            }
+            const unsigned na = __popc(__ballot_sync(kFull, active));
+            const unsigned nk = __popc(__ballot_sync(kFull, keep));
+            if (lane == 0) {
+                atomicAdd(stat_ptr(a, sys0, ST_EVAL64), (unsigned long long)na);
+                if (na - nk) atomicAdd(stat_ptr(a, sys0, ST_EXCL_EVAL), (unsigned long long)(na - nk));
+            }
+        } else if (active) {
+            if (keep) {
+                const unsigned long long k = atomicAdd((unsigned long long *)&ctl->surv_count[n], 1ull);
+                if ((long long)k < a.surv_cap) a.surv[(size_t)n * a.surv_cap + k] = sv;
+                else ctl->error = 1;
+            }
+            atomicAdd(stat_ptr(a, sys, ST_EVAL64), 1ull);
+            if (!keep) atomicAdd(stat_ptr(a, sys, ST_EXCL_EVAL), 1ull);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------
+
+static cudaError_t launch_hs(const SweepArgs &a, int n, int num_sms, cudaStream_t st) {
+    switch (n) {
+    case 1: return launch_hs_dim1(a, num_sms, st);
+    case 2: return launch_hs_dim2(a, num_sms, st);
+    case 3: return launch_hs_dim3(a, num_sms, st);
+    case 4: return launch_hs_dim4(a, num_sms, st);
+    case 5: return launch_hs_dim5(a, num_sms, st);
+    case 6: return launch_hs_dim6(a, num_sms, st);
+    case 7: return launch_hs_dim7(a, num_sms, st);
+    case 8: return launch_hs_dim8(a, num_sms, st);
+    case 9: return launch_hs_dim9(a, num_sms, st);
+    case 10: return launch_hs_dim10(a, num_sms, st);
+    case 11: return launch_hs_dim11(a, num_sms, st);
+    case 12: return launch_hs_dim12(a, num_sms, st);
+    case 13: return launch_hs_dim13(a, num_sms, st);
+    case 14: return launch_hs_dim14(a, num_sms, st);
+    case 15: return launch_hs_dim15(a, num_sms, st);
+    case 16: return launch_hs_dim16(a, num_sms, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_sweep(const SweepArgs &a, const int *hs_dims, int n_hs_dims, int eval_blocks,
+                         int eval_threads, int num_sms, cudaStream_t st, cudaEvent_t *ev) {
+    // ev (optional): n_hs_dims + 5 events recorded between the stages
+    if (ev) cudaEventRecord(ev[0], st);
+    k_wave_begin<<<1, 32, 0, st>>>(a);
+    if (ev) cudaEventRecord(ev[1], st);
+    k_eval<<<eval_blocks, eval_threads, 0, st>>>(a);
+    if (ev) cudaEventRecord(ev[2], st);
+    k_eval64<<<num_sms * 8, kEval64Threads, 0, st>>>(a);
+    if (ev) cudaEventRecord(ev[3], st);
+    for (int q = 0; q < n_hs_dims; q++) {
+        cudaError_t e = launch_hs(a, hs_dims[q], num_sms, st);
+        if (e != cudaSuccess) return e;
+        if (ev) cudaEventRecord(ev[4 + q], st);
+    }
+    k_commit<<<num_sms * 4, 256, 0, st>>>(a, a.max_fan_shift);
+    if (ev) cudaEventRecord(ev[4 + n_hs_dims], st);
+    return cudaGetLastError();
+}
+
+cudaError_t build_sweep_graph(const SweepArgs &a, const int *hs_dims, int n_hs_dims, int eval_blocks,
+                              int eval_threads, int num_sms, cudaGraph_t *out) {
+    *out = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+    cudaStream_t cs = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t le = launch_sweep(a, hs_dims, n_hs_dims, eval_blocks, eval_threads, num_sms, cs, nullptr);
+            k_loop_cond<<<1, 32, 0, cs>>>(a, h);
+            cudaGraph_t captured = nullptr;
+            e = cudaStreamEndCapture(cs, &captured);
+            if (e == cudaSuccess && le != cudaSuccess) e = le;
+        }
+    }
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return e;
+    }
+    *out = g;
+    return cudaSuccess;
+}
+
+cudaError_t launch_seed_roots(const SweepArgs &a, const double *d_box_lo, const double *d_box_hi,
+                              const int32_t *d_root_depth, int n_sys, int n_max, cudaStream_t st) {
+    int blocks = (n_sys + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    k_seed_roots<<<blocks, 256, 0, st>>>(a, d_box_lo, d_box_hi, d_root_depth, n_sys, n_max);
+    return cudaGetLastError();
+}
+
+}  // namespace ivs

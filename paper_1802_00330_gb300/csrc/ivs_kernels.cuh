@@ -1,0 +1,65 @@
+// ivs_kernels.cuh -- kernels of one sweep over the device queue, and their launchers.
+//
+// One sweep ("wave") pops up to K parent boxes from the top of the queue and runs:
+//   k_wave_begin  : chooses K so that the worst case (every child kept) fits
+//   k_eval        : one warp per parent, one lane per child box (Algorithm 2's split is
+//                   implicit: child c takes the upper half of coordinate j when bit j of
+//                   c is set); optional FP32 outward evaluation, then FP64 evaluation
+//                   (Definition 1-2); survivors compacted with a warp ballot into a list
+//                   per dimension n
+//   k_hs<N>       : one thread per survivor: Hansen-Sengupta sweep (Algorithm 3), then
+//                   accept (Algorithm 1 (II)) or write the box as a new parent
+//   k_commit      : moves the new parents onto the queue where the popped ones were
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ivs_internal.h"
+
+namespace ivs {
+
+struct SweepArgs {
+    DevTables tb;
+    DevQueue q;        // the queue
+    DevQueue stage;    // new parents of this sweep
+    DevOut out;
+    WaveCtl *ctl;
+    Surv *surv;        // survivor list of dimension n at surv + n * surv_cap
+    int64_t surv_cap;
+    Surv *cand;        // FP32 survivors (capacity surv_cap)
+    unsigned long long *stats;   // [n_sys][ST_COUNT]
+    int64_t wave_children;       // children a sweep may evaluate
+    int32_t max_fan_shift;       // max n over the plan's systems
+    int32_t n_sys;
+};
+
+// kernels per sweep: 4 + n_hs_dims; ev (nullable) receives n_hs_dims + 4 stage events
+cudaError_t launch_sweep(const SweepArgs &a, const int *hs_dims, int n_hs_dims, int eval_blocks,
+                         int eval_threads, int num_sms, cudaStream_t st, cudaEvent_t *ev);
+// The sweep loop as one CUDA graph: a conditional WHILE node whose body is one sweep
+// followed by a kernel that keeps the condition set while the queue is non-empty, no
+// error occurred and ctl->waves < ctl->wave_limit.  Kernels per iteration: 5 + n_hs_dims.
+cudaError_t build_sweep_graph(const SweepArgs &a, const int *hs_dims, int n_hs_dims, int eval_blocks,
+                              int eval_threads, int num_sms, cudaGraph_t *out);
+// directed-rounding rate microbenchmark (kind 0 FP64, 1 FP32); returns ops and fills ms
+cudaError_t run_probe(int kind, int num_sms, double *ops, float *ms);
+cudaError_t launch_seed_roots(const SweepArgs &a, const double *d_box_lo, const double *d_box_hi,
+                              const int32_t *d_root_depth, int n_sys, int n_max, cudaStream_t st);
+// Hansen-Sengupta + accept/split kernel for dimension n (ivs_hs_*.cu)
+cudaError_t launch_hs_dim1(const SweepArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_hs_dim2(const SweepArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_hs_dim3(const SweepArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_hs_dim4(const SweepArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_hs_dim5(const SweepArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_hs_dim6(const SweepArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_hs_dim7(const SweepArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_hs_dim8(const SweepArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_hs_dim9(const SweepArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_hs_dim10(const SweepArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_hs_dim11(const SweepArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_hs_dim12(const SweepArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_hs_dim13(const SweepArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_hs_dim14(const SweepArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_hs_dim15(const SweepArgs &a, int num_sms, cudaStream_t st);
+cudaError_t launch_hs_dim16(const SweepArgs &a, int num_sms, cudaStream_t st);
+
+}  // namespace ivs

@@ -1,0 +1,68 @@
+// ivs_probe.cu -- directed-rounding arithmetic rate of the device.  The roofline of the
+// solver's kernels is the FP64 (or FP32) pipe, and its rate is measured here rather than
+// taken from a datasheet: each thread runs 8 independent chains alternating a
+// round-down add and a round-up multiply, so the pipe, not latency, bounds the loop.
+#include <cuda_runtime.h>
+
+#include "ivs_kernels.cuh"
+
+namespace ivs {
+
+constexpr int kProbeIters = 4096;
+constexpr int kProbeChains = 8;
+
+__global__ void k_probe_fp64(double seed, double *sink) {
+    double x[kProbeChains];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; c++) x[c] = seed + c * 1e-3 + threadIdx.x * 1e-9;
+    const double a = 1.0000000001, b = 1e-12;
+    for (int i = 0; i < kProbeIters; i++) {
+#pragma unroll
+        for (int c = 0; c < kProbeChains; c++) x[c] = __dmul_ru(__dadd_rd(x[c], b), a);
+    }
+    double s = 0;
+#pragma unroll
+    for (int c = 0; c < kProbeChains; c++) s += x[c];
+    if (s == 12345.678) sink[0] = s;   // never true; keeps the chains live
+}
+
+__global__ void k_probe_fp32(float seed, float *sink) {
+    float x[kProbeChains];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; c++) x[c] = seed + c * 1e-3f + threadIdx.x * 1e-7f;
+    const float a = 1.0000001f, b = 1e-7f;
+    for (int i = 0; i < kProbeIters; i++) {
+#pragma unroll
+        for (int c = 0; c < kProbeChains; c++) x[c] = __fmul_ru(__fadd_rd(x[c], b), a);
+    }
+    float s = 0;
+#pragma unroll
+    for (int c = 0; c < kProbeChains; c++) s += x[c];
+    if (s == 12345.678f) sink[0] = s;
+}
+
+cudaError_t run_probe(int kind, int num_sms, double *ops, float *ms) {
+    void *sink = nullptr;
+    cudaError_t e = cudaMalloc(&sink, 64);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const int threads = 256, blocks = num_sms * 8;
+    for (int rep = 0; rep < 3; rep++) {   // first launches warm up clocks and caches
+        cudaEventRecord(a);
+        if (kind == 0) k_probe_fp64<<<blocks, threads>>>(1.0, (double *)sink);
+        else k_probe_fp32<<<blocks, threads>>>(1.0f, (float *)sink);
+        cudaEventRecord(b);
+    }
+    e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    *ops = (double)blocks * threads * kProbeIters * kProbeChains * 2.0;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    return e;
+}
+
+}  // namespace ivs

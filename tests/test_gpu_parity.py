@@ -1,0 +1,128 @@
+"""GPU path (through the C ABI) against the serial oracle, element by element.
+
+The result is a set of boxes whose fate depends only on each box, so the sorted output
+of the CUDA library must equal the oracle's bit for bit (every lo/hi double, flag and
+depth), and the processed-box counts must agree.  Paper: Algorithms 1-4, eq 10, 21-27.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+from paper_1802_00330_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_00330_gb300 import _binding, build
+    build.build()
+    _binding.load()
+    return _binding
+
+
+def assert_same(g, o, check_stats=True):
+    assert g["status"] == o["status"]
+    assert g["lo"].shape == o["lo"].shape, (g["lo"].shape, o["lo"].shape)
+    assert np.array_equal(g["lo"], o["lo"]) and np.array_equal(g["hi"], o["hi"])
+    assert np.array_equal(g["flags"], o["flags"]) and np.array_equal(g["depth"], o["depth"])
+    if check_stats:
+        gs, os_ = g["stats"], o["stats"]
+        assert gs["boxes"] == os_["boxes"]
+        assert gs["excluded_prefilter"] + gs["excluded_eval"] == os_["excluded_eval"]
+        for k in ("hs_applied", "hs_empty", "hs_contracted", "hs_singular", "accepted", "unsplittable", "split"):
+            assert gs[k] == os_[k], k
+
+
+def test_n2_config_bit_exact(gpu, orc):
+    s = synth.config_n2()
+    for pre in (0, 1):
+        g = gpu.solve(s, prefilter_fp32=pre)
+        o = orc.solve(s)
+        assert_same(g, o)
+        assert len(g["lo"]) == 2
+
+
+@pytest.mark.parametrize("hs", [0, 1])
+@pytest.mark.parametrize("pre", [0, 1])
+def test_small_planted_systems(gpu, orc, hs, pre):
+    systems = synth.config_batched(count=10, seed=777, n_range=(2, 5))
+    for s in systems:
+        g = gpu.solve(s, hs_enable=hs, prefilter_fp32=pre, tol=1e-4)
+        o = orc.solve(s, hs_enable=hs, tol=1e-4)
+        assert_same(g, o)
+
+
+def test_n6_config_bit_exact(gpu, orc):
+    s = synth.config_n6()
+    g = gpu.solve(s)
+    o = orc.solve(s)
+    assert_same(g, o)
+
+
+def test_prefilter_is_result_neutral(gpu):
+    s = synth.config_n6()
+    a = gpu.solve(s, prefilter_fp32=1)
+    b = gpu.solve(s, prefilter_fp32=0)
+    assert np.array_equal(a["lo"], b["lo"]) and np.array_equal(a["hi"], b["hi"])
+    assert a["stats"]["excluded_prefilter"] > 0
+    assert a["stats"]["excluded_prefilter"] + a["stats"]["excluded_eval"] == b["stats"]["excluded_eval"]
+
+
+def test_batch_equals_individual(gpu, orc):
+    systems = synth.config_batched(count=24, seed=4242, n_range=(2, 6))
+    outs = gpu.solve_batch(systems)
+    for s, g in zip(systems, outs):
+        assert_same(g, orc.solve(s))
+
+
+def test_many_waves_small_chunks(gpu, orc):
+    """A tiny sweep size forces many sweeps per level (depth-first chunks): same result."""
+    s = synth.config_batched(count=2, seed=99, n_range=(4, 4))[0]
+    plan = gpu.Plan([s], wave_children=64)
+    plan.run()
+    g = plan.result(0)
+    plan.close()
+    assert_same(g, orc.solve(s))
+    assert g["stats"]["waves"] > 20
+
+
+def test_paper_round_counts_on_gpu(gpu):
+    """Table 1 / Table 4 / Table 7 of the paper: boxes kept at depth 2 (round 3) of the
+    printed systems, without HS: 4847 (katsura8), 5120 (noon9), 5714 (kinema)."""
+    for name, want in (("katsura8", 4847), ("noon9", 5120), ("kinema", 5714)):
+        s = synth.load_fixture(os.path.join(GOLDEN, f"{name}.txt"))
+        g = gpu.solve(s, hs_enable=0, tol=0.0, max_depth=2)
+        assert g["status"] == 3
+        assert int(np.sum((g["flags"] & 4) == 4)) == want
+
+
+def test_edge_cases(gpu, orc):
+    # root-free system: empty result, OK
+    s = synth.parse_system(["x1^2 + x2^2 + 1", "x1 - x2"], 2, box=(-3, 3), tol=1e-6)
+    assert_same(gpu.solve(s), orc.solve(s))
+    # degenerate coordinate (lo == hi)
+    s = synth.config_n2()
+    lo, hi = np.array([-2.0, 0.5]), np.array([2.0, 0.5])
+    assert_same(gpu.solve(s, box_lo=lo, box_hi=hi, hs_enable=0), orc.solve(s, box_lo=lo, box_hi=hi, hs_enable=0))
+    # depth cut
+    assert_same(gpu.solve(s, max_depth=4), orc.solve(s, max_depth=4))
+    # root depth and a late HS start
+    assert_same(gpu.solve(s, root_depth=3, hs_min_depth=8), orc.solve(s, root_depth=3, hs_min_depth=8))
+    # several HS sweeps per visit
+    assert_same(gpu.solve(s, hs_iters=3), orc.solve(s, hs_iters=3))
+    # non-double coefficient (interval coefficient) and an equation without variables' terms
+    s = synth.parse_system(["x1^2 - 1.1", "x2 - 0.3*x1"], 2, box=(-2, 2), tol=1e-9)
+    assert_same(gpu.solve(s), orc.solve(s))
+
+
+def test_budget_flags(gpu):
+    s = synth.config_n6()
+    g = gpu.solve(s, max_boxes=5000)
+    assert g["status"] == 3
