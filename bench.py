@@ -235,6 +235,12 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
     value = boxes_all / t_dev
     sys_per_s = world * len(systems) * args.steps / t_dev
 
+    if args.only_timed:
+        if rank == 0:
+            print(json.dumps({"metric": "boxes/sec", "value": boxes_all / t_dev, "unit": "boxes/s",
+                              "ms_per_step": 1e3 * t_dev / args.steps, "only_timed": True}), flush=True)
+        plan.close()
+        return None
     # parity guard: the timed solve's result equals the warm-up solve's
     res = plan.result(0)
     assert np.array_equal(res["lo"], ref["lo"]) and np.array_equal(res["hi"], ref["hi"])
@@ -370,6 +376,8 @@ def main():
     ap.add_argument("--cpu-boxes", type=int, default=600_000)
     ap.add_argument("--ref-boxes", type=int, default=200_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-timed", action="store_true",
+                    help="time the device-resident solve only (for profiler runs)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

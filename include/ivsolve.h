@@ -71,8 +71,11 @@ typedef struct ivs_options {
     int32_t hs_enable;       /* 1: Hansen-Sengupta sweep on boxes that survive F(X)    */
     int32_t hs_min_depth;    /* sweep only at depth >= this (the paper starts late)    */
     int32_t hs_iters;        /* sweeps per visit (>= 1)                                */
-    int32_t prefilter_fp32;  /* 1: FP32 outward-rounded exclusion before FP64; it can
-                                only drop boxes FP64 drops, so results are identical   */
+    int32_t prefilter_fp32;  /* 1: FP32 stage before FP64.  It carries float enclosures
+                                of both ends of every FP64 intermediate, so it drops a
+                                box only when FP64 would and keeps one only when FP64
+                                would; undecided boxes run the FP64 evaluation.  Results
+                                are identical with and without it.                     */
     int32_t root_depth;      /* depth of the initial box                               */
     int32_t max_depth;       /* a box that would split past it is returned with
                                 IVS_BOX_DEPTH_LIMIT and status IVS_ERR_BUDGET          */
@@ -97,6 +100,7 @@ typedef struct ivs_stats {
     double device_ms;           /* device time of the solve                            */
     int64_t launches;           /* kernels the solve launched                          */
     int64_t eval64_boxes;       /* boxes that ran the FP64 evaluation                  */
+    int64_t kept_shadow;        /* boxes the FP32 shadow proved FP64 would keep        */
 } ivs_stats;
 
 typedef struct ivs_result ivs_result;
@@ -174,8 +178,10 @@ int32_t ivs_plan_kernel_times(ivs_plan *p, ivs_kernel_time *out, int32_t max);
 
 /* Microbenchmark of the directed-rounding arithmetic rate of the device (no paper
  * counterpart; it supplies the roofline denominator): kind 0 = FP64 (__dadd_rd /
- * __dmul_ru chains), kind 1 = FP32 (__fadd_rd / __fmul_ru).  Writes the rate in
- * operations per second (one add or one multiply = one operation) and the kernel time. */
+ * __dmul_ru chains), kind 1 = FP32 (__fadd_rd / __fmul_ru), kind 2 / 3 = FP64 with only
+ * 8 / 1 lanes of each warp active (counts only active-lane operations: shows whether
+ * idle lanes cost FP64 issue time).  Writes the rate in operations per second (one add
+ * or one multiply = one operation) and the kernel time. */
 int ivs_probe_rate(int32_t kind, int32_t device, double *ops_per_s, double *ms);
 
 const char *ivs_status_str(int status);

@@ -39,7 +39,8 @@ class ivs_stats(C.Structure):
                 ("hs_applied", C.c_int64), ("hs_empty", C.c_int64), ("hs_contracted", C.c_int64),
                 ("hs_singular", C.c_int64), ("accepted", C.c_int64), ("unsplittable", C.c_int64),
                 ("split", C.c_int64), ("max_depth_seen", C.c_int32), ("waves", C.c_int32),
-                ("device_ms", C.c_double), ("launches", C.c_int64), ("eval64_boxes", C.c_int64)]
+                ("device_ms", C.c_double), ("launches", C.c_int64), ("eval64_boxes", C.c_int64),
+                ("kept_shadow", C.c_int64)]
 
 
 class ivs_plan_cfg(C.Structure):

@@ -17,6 +17,7 @@
 #include "../../include/ivsolve.h"
 #include "ivs_internal.h"
 #include "ivs_kernels.cuh"
+#include "ivs_tab.cuh"
 
 using namespace ivs;
 
@@ -61,23 +62,59 @@ float to_float_up(double d) {
     return f;
 }
 
-struct HostTables {
-    std::vector<DevSys> sys;
-    std::vector<int32_t> poly_term_off{0};
+// One system's polynomials before packing into a blob (local indices).
+struct SysBuild {
+    std::vector<int32_t> poly_off{0};
     std::vector<double> clo, chi;
-    std::vector<float> clo32, chi32;
-    std::vector<int32_t> fac_off{0};
+    std::vector<uint32_t> tinfo;
     std::vector<uint8_t> fac;
 };
 
-void add_term(HostTables &h, double clo, double chi, const uint8_t *e, int n) {
-    h.clo.push_back(clo);
-    h.chi.push_back(chi);
-    h.clo32.push_back(to_float_down(clo));
-    h.chi32.push_back(to_float_up(chi));
+struct HostTables {
+    std::vector<DevSys> sys;
+    std::vector<char> blobs;   // 16-byte aligned blobs (layout: ivs_tab.cuh)
+};
+
+void add_term(SysBuild &b, double clo, double chi, const uint8_t *e, int n) {
+    b.clo.push_back(clo);
+    b.chi.push_back(chi);
+    const uint32_t start = (uint32_t)b.fac.size();
+    uint32_t cnt = 0;
     for (int j = 0; j < n; j++)
-        if (e[j]) h.fac.push_back((uint8_t)((j << 4) | e[j]));
-    h.fac_off.push_back((int32_t)h.fac.size());
+        if (e[j]) {
+            b.fac.push_back((uint8_t)((j << 4) | e[j]));
+            cnt++;
+        }
+    b.tinfo.push_back((start << 5) | cnt);
+}
+
+// packs a built system into the blob arena and fills the blob fields of d
+void pack_blob(HostTables &h, const SysBuild &b, DevSys &d) {
+    const int T = (int)b.clo.size(), P = (int)b.poly_off.size() - 1, F = (int)b.fac.size();
+    const BlobLayout L = blob_layout(T, P, F);
+    const size_t off = h.blobs.size();
+    h.blobs.resize(off + L.bytes, 0);
+    char *base = h.blobs.data() + off;
+    for (int t = 0; t < T; t++) {
+        const float4 cs = make_float4(to_float_down(b.clo[t]), to_float_up(b.clo[t]), to_float_down(b.chi[t]),
+                                      to_float_up(b.chi[t]));
+        std::memcpy(base + L.cs + 16u * t, &cs, 16);
+        const float c32[2] = {to_float_down(b.clo[t]), to_float_up(b.chi[t])};
+        std::memcpy(base + L.clo32 + 4u * t, &c32[0], 4);
+        std::memcpy(base + L.chi32 + 4u * t, &c32[1], 4);
+    }
+    if (T) {
+        std::memcpy(base + L.clo, b.clo.data(), 8u * T);
+        std::memcpy(base + L.chi, b.chi.data(), 8u * T);
+        std::memcpy(base + L.tinfo, b.tinfo.data(), 4u * T);
+    }
+    std::memcpy(base + L.poly_off, b.poly_off.data(), 4u * (P + 1));
+    if (F) std::memcpy(base + L.fac, b.fac.data(), (size_t)F);
+    d.blob_off = (int64_t)off;
+    d.n_terms = T;
+    d.n_polys = P;
+    d.n_facs = F;
+    d.blob_bytes = (int32_t)L.bytes;
 }
 
 int validate(const ivs_system *s, const double *lo, const double *hi, const ivs_options *o) {
@@ -110,22 +147,44 @@ int validate(const ivs_system *s, const double *lo, const double *hi, const ivs_
 // F_i and J_ij polynomials of one system appended to the tables.  J_ij = sum over terms t
 // of equation i with a_tj > 0 of [down(c_lo a_tj), up(c_hi a_tj)] x^(a_t - e_j), in term
 // order; its factors keep the variable order of the term.
+// The FP32 shadow may decide boxes only when no FP32 intermediate can overflow: every
+// term's magnitude over the initial box, times the number of terms, stays below 1e30
+// (float max ~3.4e38).  Otherwise the plain FP32 prefilter (sound under overflow) runs.
+bool shadow_safe(const ivs_system *s, const double *lo, const double *hi) {
+    const int n = s->n_vars;
+    for (int i = 0; i < s->n_eqs; i++) {
+        const int nt = s->eq_offsets[i + 1] - s->eq_offsets[i];
+        for (int t = s->eq_offsets[i]; t < s->eq_offsets[i + 1]; t++) {
+            double c = std::max(std::fabs(s->coef_lo[t]), std::fabs(s->coef_hi ? s->coef_hi[t] : s->coef_lo[t]));
+            double b = c;
+            for (int j = 0; j < n; j++) {
+                const int a = s->exps[(size_t)t * n + j];
+                const double m = std::max(std::fabs(lo[j]), std::fabs(hi[j]));
+                for (int q = 0; q < a; q++) b *= std::max(m, 1.0);
+            }
+            if (!(b * (nt + 1) < 1e30)) return false;
+        }
+    }
+    return true;
+}
+
 void compile_system(HostTables &h, const ivs_system *s, const ivs_options *o) {
     const int n = s->n_vars, m = s->n_eqs;
+    SysBuild bld;
     DevSys d{};
     d.n = n;
     d.m = m;
-    d.f_poly = (int32_t)h.poly_term_off.size() - 1;
+    d.f_poly = 0;
     for (int i = 0; i < m; i++) {
         for (int t = s->eq_offsets[i]; t < s->eq_offsets[i + 1]; t++) {
             double clo = s->coef_lo[t], chi = s->coef_hi ? s->coef_hi[t] : clo;
-            add_term(h, clo, chi, s->exps + (size_t)t * n, n);
+            add_term(bld, clo, chi, s->exps + (size_t)t * n, n);
         }
-        h.poly_term_off.push_back((int32_t)h.clo.size());
+        bld.poly_off.push_back((int32_t)bld.clo.size());
     }
     d.j_poly = -1;
     if (m == n) {
-        d.j_poly = (int32_t)h.poly_term_off.size() - 1;
+        d.j_poly = m;
         uint8_t e[kMaxVars];
         for (int i = 0; i < m; i++)
             for (int j = 0; j < n; j++) {
@@ -135,9 +194,9 @@ void compile_system(HostTables &h, const ivs_system *s, const ivs_options *o) {
                     double clo = s->coef_lo[t], chi = s->coef_hi ? s->coef_hi[t] : clo;
                     std::memcpy(e, a, (size_t)n);
                     e[j] -= 1;
-                    add_term(h, mul_down(clo, (double)a[j]), mul_up(chi, (double)a[j]), e, n);
+                    add_term(bld, mul_down(clo, (double)a[j]), mul_up(chi, (double)a[j]), e, n);
                 }
-                h.poly_term_off.push_back((int32_t)h.clo.size());
+                bld.poly_off.push_back((int32_t)bld.clo.size());
             }
     }
     d.tol = o->tol + 0.0;   // -0 -> +0
@@ -146,7 +205,9 @@ void compile_system(HostTables &h, const ivs_system *s, const ivs_options *o) {
     d.hs_iters = o->hs_iters > 0 ? o->hs_iters : 1;
     d.max_depth = o->max_depth;
     d.prefilter = o->prefilter_fp32 ? 1 : 0;
+    d.shadow = 0;
     d.max_boxes = o->max_boxes;
+    pack_blob(h, bld, d);
     h.sys.push_back(d);
 }
 
@@ -336,6 +397,8 @@ int ivs_plan_create(int32_t n_sys, const ivs_system *systems, const double *cons
         if (std::find(p->dims.begin(), p->dims.end(), systems[s].n_vars) == p->dims.end())
             p->dims.push_back(systems[s].n_vars);
         compile_system(h, &systems[s], o);
+        h.sys.back().shadow = (o->prefilter_fp32 && std::getenv("IVS_NO_SHADOW") == nullptr &&
+                               shadow_safe(&systems[s], box_lo[s], box_hi[s])) ? 1 : 0;
         if (o->time_budget_s > 0)
             p->time_budget_s = p->time_budget_s > 0 ? std::min(p->time_budget_s, o->time_budget_s) : o->time_budget_s;
     }
@@ -403,25 +466,20 @@ int ivs_plan_create(int32_t n_sys, const ivs_system *systems, const double *cons
     p->queue_cap = Q;
     p->out_cap = out_cap;
 
-    // tables
-    size_t tbytes = 0;
-    auto acc = [&](size_t b) { tbytes += align_up(std::max<size_t>(b, 1), 256); };
-    acc(h.sys.size() * sizeof(DevSys));
-    acc(h.poly_term_off.size() * 4);
-    acc(h.clo.size() * 8);
-    acc(h.chi.size() * 8);
-    acc(h.clo32.size() * 4);
-    acc(h.chi32.size() * 4);
-    acc(h.fac_off.size() * 4);
-    acc(h.fac.size());
-    CUDA_TRY(cudaMalloc(&p->tables_mem, tbytes));
-    void *cur = p->tables_mem;
-    int rc = 0;
-    if ((rc = upload(cur, h.sys, a.tb.sys, p->stream)) || (rc = upload(cur, h.poly_term_off, a.tb.poly_term_off, p->stream)) ||
-        (rc = upload(cur, h.clo, a.tb.term_clo, p->stream)) || (rc = upload(cur, h.chi, a.tb.term_chi, p->stream)) ||
-        (rc = upload(cur, h.clo32, a.tb.term_clo32, p->stream)) || (rc = upload(cur, h.chi32, a.tb.term_chi32, p->stream)) ||
-        (rc = upload(cur, h.fac_off, a.tb.term_fac_off, p->stream)) || (rc = upload(cur, h.fac, a.tb.fac, p->stream)))
-        return rc;
+    // tables: the DevSys array and the blob arena in one allocation
+    const size_t sys_bytes = align_up(h.sys.size() * sizeof(DevSys), 256);
+    CUDA_TRY(cudaMalloc(&p->tables_mem, sys_bytes + std::max<size_t>(h.blobs.size(), 16)));
+    CUDA_TRY(cudaMemcpyAsync(p->tables_mem, h.sys.data(), h.sys.size() * sizeof(DevSys), cudaMemcpyHostToDevice,
+                             p->stream));
+    if (!h.blobs.empty())
+        CUDA_TRY(cudaMemcpyAsync((char *)p->tables_mem + sys_bytes, h.blobs.data(), h.blobs.size(),
+                                 cudaMemcpyHostToDevice, p->stream));
+    a.tb.sys = (const DevSys *)p->tables_mem;
+    a.tb.blobs = (const char *)p->tables_mem + sys_bytes;
+    // one system: every kernel caches its blob in shared memory (if it fits)
+    a.single = (n_sys == 1 && h.sys[0].blob_bytes <= 48 * 1024) ? 1 : 0;
+    a.blob_smem = a.single ? h.sys[0].blob_bytes : 0;
+    CUDA_TRY(configure_eval_kernels(a.blob_smem));
     CUDA_TRY(cudaMemcpyAsync(p->d_box_lo, roots_lo.data(), roots_lo.size() * 8, cudaMemcpyHostToDevice, p->stream));
     CUDA_TRY(cudaMemcpyAsync(p->d_box_hi, roots_hi.data(), roots_hi.size() * 8, cudaMemcpyHostToDevice, p->stream));
     CUDA_TRY(cudaMemcpyAsync(p->d_root_depth, root_depth.data(), root_depth.size() * 4, cudaMemcpyHostToDevice, p->stream));
@@ -543,6 +601,7 @@ static void fill_stats(const ivs_plan *p, int s, ivs_stats *st) {
     st->split += (int64_t)v[ST_SPLIT];
     st->max_depth_seen = std::max(st->max_depth_seen, (int32_t)v[ST_MAX_DEPTH]);
     st->eval64_boxes += (int64_t)v[ST_EVAL64];
+    st->kept_shadow += (int64_t)v[ST_KEEP_SHADOW];
     st->waves = (int32_t)p->h_ctl->waves;
     st->device_ms = p->last_ms;
     st->launches = p->launches;
@@ -631,7 +690,7 @@ int32_t ivs_plan_kernel_times(ivs_plan *p, ivs_kernel_time *out, int32_t max) {
 }
 
 int ivs_probe_rate(int32_t kind, int32_t device, double *ops_per_s, double *ms) {
-    if (!ops_per_s || (kind != 0 && kind != 1)) return fail(IVS_ERR_INVALID, "bad arguments");
+    if (!ops_per_s || kind < 0 || kind > 3) return fail(IVS_ERR_INVALID, "bad arguments");
     CUDA_TRY(cudaSetDevice(device));
     int sms = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));

@@ -1,14 +1,23 @@
-// ivs_hs.cuh -- Hansen-Sengupta sweep and the accept / split step, one thread per box
-// that survived the evaluation (Section 2.3 eq 14, 17-22; Algorithm 3; Gauss-Jordan of
+// ivs_hs.cuh -- Hansen-Sengupta sweep and the accept / split step for the boxes that
+// survived the evaluation (Section 2.3 eq 14, 17-22; Algorithm 3; Gauss-Jordan of
 // Section 2.4; Algorithm 4 products; Algorithm 1 termination (II); Algorithm 2 split).
-// Templated on the dimension n; the instantiations are spread over several translation
-// units (ivs_hs_*.cu) so that they compile in parallel.
+//
+// Mapping: one thread per box, 32 boxes per warp taken from an atomic cursor so a
+// sweep's boxes spread over every SM.  GB300's FP64 pipe retires 2 lane-operations per
+// cycle per SM and charges a whole warp instruction whatever the number of active
+// lanes, so every lane of every FP64 instruction carries a different box; two or three
+// resident warps per SM already keep the pipe busy.  Matrices live in per-thread shared
+// memory (structure of arrays, conflict-free); the system's term table is cached in
+// shared memory when the plan holds one system.  Comparisons, sign tests, NaN and
+// finiteness checks run on the integer pipes.  Templated on n; the instantiations are
+// spread over several translation units (ivs_hs_*.cu).
 #pragma once
 #include <cuda_runtime.h>
 
 #include "ivs_internal.h"
 #include "ivs_interval.cuh"
 #include "ivs_kernels.cuh"
+#include "ivs_tab.cuh"
 
 namespace ivs {
 
@@ -19,98 +28,89 @@ __device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1
 __device__ __forceinline__ unsigned long long *stat_ptr(const SweepArgs &a, int sys, int slot) {
     return a.stats + (size_t)sys * ST_COUNT + slot;
 }
-}  // namespace hsd
-using hsd::kFull;
-using hsd::lane_id;
-using hsd::lanemask_lt;
-using hsd::stat_ptr;
+__device__ __forceinline__ double midpoint_rn(double lo, double hi) { return __dmul_rn(0.5, __dadd_rn(lo, hi)); }
+// integer-pipe predicates on doubles
+__device__ __forceinline__ bool d_isnan(double x) {
+    return (__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL) > 0x7FF0000000000000LL;
+}
+__device__ __forceinline__ bool d_finite(double x) {
+    return (__double_as_longlong(x) & 0x7FF0000000000000LL) != 0x7FF0000000000000LL;
+}
+// |x| as an ordered integer; NaN ranks below everything (never chosen as a pivot)
+__device__ __forceinline__ long long d_abskey(double x) {
+    const long long m = __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL;
+    return m > 0x7FF0000000000000LL ? -1 : m;
+}
+// numeric a <= b for non-NaN doubles (-0 == +0)
+__device__ __forceinline__ bool d_le(double a, double b) {
+    return d_key(a) <= d_key(b) || (d_iszero(a) && d_iszero(b));
+}
 
-// ------------------------------------------------------------------------------------
-// Hansen-Sengupta sweep + accept / split, one thread per surviving box
-// ------------------------------------------------------------------------------------
-
-// per-thread scratch in shared memory, element e of this thread at base[e * T]
+// per-thread scratch (doubles, structure of arrays with the block's thread stride T)
+template <int N>
 struct Scratch {
-    double *J;     // 2 N N : J (then M) entry (i,j): lo at 2(iN+j), hi at 2(iN+j)+1
-    double *G;     // N N   : Gauss-Jordan working matrix, then B
-    double *X;     // 2 N   : box handed to the polynomial interpreter
-    int *rowid;    // 2 N   : row ids during elimination, then column slots
-    int T;
+    static constexpr int J = 0;              // 2 N N : J(X), then M = B J
+    static constexpr int G = 2 * N * N;      // N N   : Gauss-Jordan matrix, then B
+    static constexpr int X = 3 * N * N;      // 2 N   : box for the interpreter
+    static constexpr int DOUBLES = X + 2 * N;
+    static constexpr int INTS = 2 * N;       // row ids, then column slots
+    static constexpr size_t BYTES = (size_t)DOUBLES * 8 + (size_t)INTS * 4;
 };
 
-// interval value of polynomial p over the box in scratch X (runtime variable indices)
-static __device__ __forceinline__ ivd eval_poly_scratch(const DevTables &tb, int p, const double *X, int T) {
-    const int t0 = tb.poly_term_off[p], t1 = tb.poly_term_off[p + 1];
-    ivd acc = {0.0, 0.0};
-    for (int t = t0; t < t1; t++) {
-        const ivd cf = {tb.term_clo[t], tb.term_chi[t]};
-        const int f0 = tb.term_fac_off[t], f1 = tb.term_fac_off[t + 1];
-        ivd v;
-        if (f0 == f1) {
-            v = cf;
-        } else {
-            unsigned fc = tb.fac[f0];
-            unsigned j = fc >> 4;
-            ivd prod = iv_pow(ivd{X[(2 * j) * T], X[(2 * j + 1) * T]}, (int)(fc & 15u));
-            for (int f = f0 + 1; f < f1; f++) {
-                fc = tb.fac[f];
-                j = fc >> 4;
-                prod = iv_mul(prod, iv_pow(ivd{X[(2 * j) * T], X[(2 * j + 1) * T]}, (int)(fc & 15u)));
-            }
-            v = iv_mul(cf, prod);
-        }
-        acc = (t == t0) ? v : iv_add(acc, v);
-    }
-    return acc;
-}
-
-static __device__ __forceinline__ double midpoint_rn(double lo, double hi) {
-    return __dmul_rn(0.5, __dadd_rn(lo, hi));
-}
+struct BoxS {
+    const double *X;
+    int T;
+    __device__ __forceinline__ ivd operator()(unsigned j) const { return ivd{X[(2 * j) * T], X[(2 * j + 1) * T]}; }
+};
+}  // namespace hsd
 
 // One Gauss-Seidel sweep on B f(x) + B J(X)(z - x) = 0 (eq 14, 21, 22).
 // Returns 0 (Xo written), 1 (empty), 2 (skipped: singular preconditioner).
 template <int N>
-__device__ int hs_sweep(const DevTables &tb, const DevSys &S, const double *Xlo, const double *Xhi,
-                        double *Xolo, double *Xohi, const Scratch &sc) {
-    const int T = sc.T;
-    double *X = sc.X;
-    double *J = sc.J;
-    double *G = sc.G;
-    int *rowid = sc.rowid;
+__device__ int hs_sweep(const SysTab &Tb, const DevSys &S, const double *Xlo, const double *Xhi,
+                        double *Xolo, double *Xohi, double *sm, int *smi, int T) {
+    using namespace hsd;
+    using L = Scratch<N>;
+    double *J = sm + L::J * T;
+    double *G = sm + L::G * T;
+    double *X = sm + L::X * T;
+    int *rowid = smi;
+    int *slot_of = smi + N * T;
 #pragma unroll
     for (int j = 0; j < N; j++) {
         X[(2 * j) * T] = Xlo[j];
         X[(2 * j + 1) * T] = Xhi[j];
     }
-    // J(X): derivative polynomials compiled on the host
+    // J(X) from the derivative polynomials compiled on the host
     for (int q = 0; q < N * N; q++) {
-        const ivd v = eval_poly_scratch(tb, S.j_poly + q, X, T);
+        const ivd v = poly64(Tb, S.j_poly + q, BoxS{X, T});
         J[(2 * q) * T] = v.lo;
         J[(2 * q + 1) * T] = v.hi;
     }
-    // A = mid(J(X)) (round to nearest)
+    // A = mid(J(X)), round to nearest
     bool bad = false;
     for (int q = 0; q < N * N; q++) {
         const double m = midpoint_rn(J[(2 * q) * T], J[(2 * q + 1) * T]);
-        bad |= !isfinite(m);
+        bad |= !d_finite(m);
         G[q * T] = m;
     }
     if (bad) return 2;
-    // Gauss-Jordan with partial pivoting (Section 2.4), in place: after step k, storage
-    // column k holds column rowid[k] of the right half [.|I] (the classic in-place form;
-    // entries of untouched identity columns are 0 and their updates are exact no-ops).
+    // Gauss-Jordan with partial pivoting (Section 2.4), in place: after step k storage
+    // column k holds column rowid[k] of the right half [.|I]; entries of identity columns
+    // not yet touched are 0 and their updates are exact no-ops, so they are skipped
 #pragma unroll
     for (int k = 0; k < N; k++) rowid[k * T] = k;
     for (int k = 0; k < N; k++) {
         int piv = k;
-        double best = fabs(G[(k * N + k) * T]);
+        long long best = d_abskey(G[(k * N + k) * T]);
+        if (best < 0) return 2;            // NaN diagonal: the serial search keeps it, singular
         for (int i = k + 1; i < N; i++) {
-            const double v = fabs(G[(i * N + k) * T]);
+            const long long v = d_abskey(G[(i * N + k) * T]);
             if (v > best) { best = v; piv = i; }
         }
-        if (!(best > 0.0) || !isfinite(best)) return 2;
+        if (best <= 0 || best >= 0x7FF0000000000000LL) return 2;   // zero, NaN or infinite
         if (piv != k) {
+#pragma unroll
             for (int j = 0; j < N; j++) {
                 const double t = G[(k * N + j) * T];
                 G[(k * N + j) * T] = G[(piv * N + j) * T];
@@ -121,20 +121,22 @@ __device__ int hs_sweep(const DevTables &tb, const DevSys &S, const double *Xlo,
             rowid[piv * T] = t;
         }
         const double pv = G[(k * N + k) * T];
-        const double rp = __ddiv_rn(1.0, pv);       // eq 23 on the identity column
+        const double rp = __ddiv_rn(1.0, pv);                           // eq 23 (identity column)
+#pragma unroll
         for (int j = 0; j < N; j++)
             if (j != k) G[(k * N + j) * T] = __ddiv_rn(G[(k * N + j) * T], pv);   // eq 23
         G[(k * N + k) * T] = rp;
-        for (int i = 0; i < N; i++) {                                          // eq 24
+        for (int i = 0; i < N; i++) {                                  // eq 24
             if (i == k) continue;
             const double f = G[(i * N + k) * T];
+#pragma unroll
             for (int j = 0; j < N; j++)
                 if (j != k) G[(i * N + j) * T] = __dsub_rn(G[(i * N + j) * T], __dmul_rn(f, G[(k * N + j) * T]));
             G[(i * N + k) * T] = __dsub_rn(0.0, __dmul_rn(f, rp));
         }
     }
-    // storage column k is column rowid[k] of B: slot_of[u] = k with rowid[k] = u
-    int *slot_of = rowid + N * T;
+    // storage column k is column rowid[k] of B: restore the column order
+#pragma unroll
     for (int k = 0; k < N; k++) slot_of[rowid[k * T] * T] = k;
     for (int i = 0; i < N; i++) {
         double rowv[N];
@@ -142,7 +144,7 @@ __device__ int hs_sweep(const DevTables &tb, const DevSys &S, const double *Xlo,
         for (int u = 0; u < N; u++) rowv[u] = G[(i * N + slot_of[u * T]) * T];
 #pragma unroll
         for (int u = 0; u < N; u++) {
-            if (!isfinite(rowv[u])) bad = true;
+            bad |= !d_finite(rowv[u]);
             G[(i * N + u) * T] = rowv[u];
         }
     }
@@ -156,9 +158,9 @@ __device__ int hs_sweep(const DevTables &tb, const DevSys &S, const double *Xlo,
         X[(2 * j + 1) * T] = xc[j];
     }
     ivd fx[N];
-#pragma unroll
-    for (int i = 0; i < N; i++) fx[i] = eval_poly_scratch(tb, S.f_poly + i, X, T);
-    // M = B J(X) in place of J (column by column), r = B f(x) (Algorithm 4, outward)
+    for (int i = 0; i < N; i++) fx[i] = poly64(Tb, S.f_poly + i, BoxS{X, T});
+    // M = B J(X) in place of J, column by column; r = B f(x) (Algorithm 4, outward,
+    // u = 1..n in order; starting from the first product equals starting from [0,0])
     for (int j = 0; j < N; j++) {
         ivd col[N];
 #pragma unroll
@@ -193,7 +195,7 @@ __device__ int hs_sweep(const DevTables &tb, const DevSys &S, const double *Xlo,
             s = iv_add(s, iv_mul(mij, d));
         }
         const ivd D = {J[(2 * (i * N + i)) * T], J[(2 * (i * N + i) + 1) * T]};
-        if (isnan(s.lo) || isnan(s.hi) || isnan(D.lo) || isnan(D.hi)) continue;
+        if (d_isnan(s.lo) || d_isnan(s.hi) || d_isnan(D.lo) || d_isnan(D.hi)) continue;
         ivd pc[2];
         const int np = iv_extdiv(s, D, pc);
         double lo = 0.0, hi = 0.0;
@@ -201,7 +203,7 @@ __device__ int hs_sweep(const DevTables &tb, const DevSys &S, const double *Xlo,
         for (int q = 0; q < np; q++) {
             const ivd Y = iv_sub(ivd{xc[i], xc[i]}, pc[q]);
             const double a0 = d_max(Xlo[i], Y.lo), b0 = d_min(Xhi[i], Y.hi);
-            if (d_key(a0) <= d_key(b0) || a0 == b0) {
+            if (d_le(a0, b0)) {
                 lo = any ? d_min(lo, a0) : a0;
                 hi = any ? d_max(hi, b0) : b0;
                 any = true;
@@ -215,18 +217,23 @@ __device__ int hs_sweep(const DevTables &tb, const DevSys &S, const double *Xlo,
 }
 
 template <int N>
-__global__ void __launch_bounds__(64) k_hs(SweepArgs a) {
-    extern __shared__ double smem[];
+__global__ void __launch_bounds__(128) k_hs(SweepArgs a) {
+    using namespace hsd;
+    using L = Scratch<N>;
+    extern __shared__ __align__(16) char smem[];
     const int T = blockDim.x, tid = threadIdx.x;
-    Scratch sc;
-    sc.T = T;
-    sc.J = smem + tid;
-    sc.G = smem + (size_t)2 * N * N * T + tid;
-    sc.X = smem + (size_t)3 * N * N * T + tid;
-    sc.rowid = reinterpret_cast<int *>(smem + (size_t)(3 * N * N + 2 * N) * T) + tid;
+    const size_t blob_bytes = a.single ? (size_t)a.blob_smem : 0;
+    double *sm = reinterpret_cast<double *>(smem + blob_bytes) + tid;
+    int *smi = reinterpret_cast<int *>(reinterpret_cast<double *>(smem + blob_bytes) + (size_t)L::DOUBLES * T) + tid;
 
     WaveCtl *ctl = a.ctl;
     const int64_t count = ctl->surv_count[N];
+    if (count == 0) return;
+    if (a.single) {
+        const DevSys &S0 = a.tb.sys[0];
+        copy_blob(smem, a.tb.blobs + S0.blob_off, (uint32_t)S0.blob_bytes);
+        __syncthreads();
+    }
     const Surv *list = a.surv + (size_t)N * a.surv_cap;
     const unsigned lane = lane_id();
     for (;;) {
@@ -237,7 +244,7 @@ __global__ void __launch_bounds__(64) k_hs(SweepArgs a) {
         if ((long long)ws >= count) break;
         const int64_t idx = (int64_t)ws + lane;
         const bool active = idx < count;
-        int fate = 0;   // 0 none/dropped, 1 accepted, 2 new parent
+        int fate = 0;   // 0 none / dropped, 1 accepted, 2 new parent
         int flag = 0, sys = 0, depth = 0;
         double Xlo[N], Xhi[N], xm[N];
         unsigned st_app = 0, st_empty = 0, st_con = 0, st_sing = 0, st_uns = 0;
@@ -249,6 +256,7 @@ __global__ void __launch_bounds__(64) k_hs(SweepArgs a) {
             const bool root = (meta & kRootFlag) != 0;
             depth = (int)(meta & kDepthMask) + (root ? 0 : 1);
             const DevSys S = a.tb.sys[sys];
+            const SysTab Tb = make_tab(a.single ? smem : a.tb.blobs + S.blob_off, S);
 #pragma unroll
             for (int j = 0; j < N; j++) {
                 const bool up = (sv.child >> j) & 1u;
@@ -261,13 +269,14 @@ __global__ void __launch_bounds__(64) k_hs(SweepArgs a) {
                 for (int it = 0; it < iters; it++) {
                     st_app++;
                     double Ylo[N], Yhi[N];
-                    const int rc = hs_sweep<N>(a.tb, S, Xlo, Xhi, Ylo, Yhi, sc);
+                    const int rc = hs_sweep<N>(Tb, S, Xlo, Xhi, Ylo, Yhi, sm, smi, T);
                     if (rc == 1) { dropped = true; break; }
                     if (rc == 2) { st_sing++; break; }
                     bool changed = false;
 #pragma unroll
                     for (int j = 0; j < N; j++) {
-                        changed |= (Ylo[j] != Xlo[j]) || (Yhi[j] != Xhi[j]);
+                        changed |= (__double_as_longlong(Ylo[j]) != __double_as_longlong(Xlo[j]) && !(d_iszero(Ylo[j]) && d_iszero(Xlo[j]))) ||
+                                   (__double_as_longlong(Yhi[j]) != __double_as_longlong(Xhi[j]) && !(d_iszero(Yhi[j]) && d_iszero(Xhi[j])));
                         Xlo[j] = Ylo[j];
                         Xhi[j] = Yhi[j];
                     }
@@ -295,7 +304,11 @@ __global__ void __launch_bounds__(64) k_hs(SweepArgs a) {
 #pragma unroll
                     for (int j = 1; j < N; j++)
                         if (j == jw) { mw = xm[j]; lw = Xlo[j]; hw = Xhi[j]; }
-                    if (mw == lw || mw == hw) {
+                    if (d_le(mw, lw) && d_le(lw, mw)) {
+                        fate = 1;
+                        flag = 2;
+                        st_uns++;
+                    } else if (d_le(mw, hw) && d_le(hw, mw)) {
                         fate = 1;
                         flag = 2;
                         st_uns++;
@@ -376,27 +389,32 @@ __global__ void __launch_bounds__(64) k_hs(SweepArgs a) {
 
 // ---- launcher -------------------------------------------------------------------
 
-inline size_t hs_smem_for_(int n, int threads) {
-    return (size_t)threads * ((size_t)(3 * n * n + 2 * n) * sizeof(double) + (size_t)2 * n * sizeof(int));
-}
-
-inline int hs_threads_for_(int n) {
-    // small blocks (1-2 warps) spread a sweep's few boxes over all SMs
-    return hs_smem_for_(n, 64) <= 110 * 1024 ? 64 : 32;
+// threads per block: as many (up to 128) as keep the block within ~200 KB of shared memory
+template <int N>
+inline int hs_threads(size_t blob) {
+    const size_t per = hsd::Scratch<N>::BYTES;
+    int t = (int)(((200u * 1024u) - blob) / per);
+    t = (t / 32) * 32;
+    if (t > 128) t = 128;
+    if (t < 32) t = 32;
+    return t;
 }
 
 template <int N>
 static cudaError_t launch_hs_n(const SweepArgs &a, int num_sms, cudaStream_t st) {
-    static int per_sm = 0;   // blocks per SM, found once per process (one device)
-    const int T = hs_threads_for_(N);
-    const size_t smem = hs_smem_for_(N, T);
-    if (per_sm == 0) {
+    static int per_sm = 0;             // blocks per SM, found once per configuration
+    static size_t configured_smem = 0;
+    const size_t blob = a.single ? (size_t)a.blob_smem : 0;
+    const int T = hs_threads<N>(blob);
+    const size_t smem = blob + (size_t)T * hsd::Scratch<N>::BYTES;
+    if (per_sm == 0 || configured_smem != smem) {
         cudaError_t e = cudaFuncSetAttribute(k_hs<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        int b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_hs<N>, T, smem);
+        int bl = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, k_hs<N>, T, smem);
         if (e != cudaSuccess) return e;
-        per_sm = b < 1 ? 1 : b;
+        per_sm = bl < 1 ? 1 : bl;
+        configured_smem = smem;
     }
     k_hs<N><<<num_sms * per_sm, T, smem, st>>>(a);
     return cudaGetLastError();

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <vector_types.h>
 
 namespace ivs {
 
@@ -28,33 +29,30 @@ enum Stat : int {
     ST_MAX_DEPTH,
     ST_FLAGS,          // bit 0: results overflowed, bit 1: depth cut, bit 2: box budget hit
     ST_EVAL64,         // boxes that ran the FP64 evaluation
+    ST_KEEP_SHADOW,    // boxes the FP32 shadow proved kept (no FP64 evaluation)
     ST_COUNT
 };
 constexpr int64_t kFlagResultOverflow = 1, kFlagDepthCut = 2, kFlagBudget = 4;
 
-// Compiled system, resident on the device.  Polynomials (F_i, then J_ij row-major) index
-// a shared term table; each term is a coefficient interval and a list of factors
-// (var << 4 | exponent), exponents >= 1.
+// Compiled system, resident on the device.  Its polynomials (the m equations F_i, then
+// the m*n Jacobian entries J_ij row-major when m == n) live in one blob of the blob
+// arena at blob_off (layout: ivs_tab.cuh).
 struct DevSys {
     int32_t n, m;
-    int32_t f_poly;        // first polynomial of F (m of them)
-    int32_t j_poly;        // first polynomial of J (m * n of them), -1 if none
+    int32_t f_poly;        // first polynomial of F (local index, 0)
+    int32_t j_poly;        // first polynomial of J (local index m), -1 if none
     double tol;
     int32_t hs_enable, hs_min_depth, hs_iters, max_depth;
     int32_t prefilter;
-    int32_t pad;
+    int32_t shadow;        // FP32 shadow decisions allowed (no FP32 overflow possible)
     int64_t max_boxes;
+    int64_t blob_off;      // byte offset of the system's blob
+    int32_t n_terms, n_polys, n_facs, blob_bytes;
 };
 
 struct DevTables {
     const DevSys *sys;
-    const int32_t *poly_term_off;   // [n_polys + 1]
-    const double *term_clo;          // [n_terms]
-    const double *term_chi;
-    const float *term_clo32;         // outward float copies of the coefficients
-    const float *term_chi32;
-    const int32_t *term_fac_off;     // [n_terms + 1]
-    const uint8_t *fac;              // [n_factors]
+    const char *blobs;     // blob arena (16-byte aligned blobs)
 };
 
 // Queue of parent boxes (boxes to split), structure of arrays with capacity `cap`:

@@ -163,4 +163,85 @@ __device__ __forceinline__ ivf fv_pow(ivf x, int k) {
     return {lo, hi};
 }
 
+// ---- FP32 shadow of an FP64 interval computation -----------------------------------
+// For an FP64 interval [L, H] the shadow holds float enclosures L in [ld, lu] and
+// H in [hd, hu].  rd32 <= rd64 and ru64 <= ru32 pointwise, and all roundings are
+// monotone, so each shadow operation below encloses the FP64 operation's result.  An
+// operation whose FP64 sign case cannot be proven from the enclosures (an end within
+// float rounding of 0 but not exactly 0) marks the shadow ambiguous ("poisoned").
+struct shv { float ld, lu, hd, hu; };
+
+__device__ __forceinline__ shv sh_add(shv a, shv b) {
+    return {__fadd_rd(a.ld, b.ld), __fadd_ru(a.lu, b.lu), __fadd_rd(a.hd, b.hd), __fadd_ru(a.hu, b.hu)};
+}
+
+// enclosure [rd(min), ru(max)] of the exact product of two values with enclosures
+// [ad, au] and [bd, bu]
+__device__ __forceinline__ float2 enc_mul(float ad, float au, float bd, float bu) {
+    const ivf r = fv_mul(ivf{ad, au}, ivf{bd, bu});
+    return make_float2(r.lo, r.hi);
+}
+
+// sign class of an FP64 interval from its shadow: 1 = [L,H] >= 0 (L >= 0),
+// 2 = [L,H] <= 0 (H <= 0), 3 = L < 0 < H, 0 = not provable
+__device__ __forceinline__ int sh_class(const shv &x) {
+    if (x.ld >= 0.0f) return 1;
+    if (x.hu <= 0.0f) return 2;
+    if (x.lu < 0.0f && x.hd > 0.0f) return 3;
+    return 0;
+}
+
+// FP64 product: L = rd64(min of the 4 end products), H = ru64(max); the proven sign
+// classes name the products that are the min and the max.
+__device__ __forceinline__ shv sh_mul(shv x, shv y, bool &poison) {
+    const int cx = sh_class(x), cy = sh_class(y);
+    if (cx == 0 || cy == 0) { poison = true; return {0.f, 0.f, 0.f, 0.f}; }
+    float2 l, h;
+    if (cx == 1) {
+        if (cy == 1) { l = enc_mul(x.ld, x.lu, y.ld, y.lu); h = enc_mul(x.hd, x.hu, y.hd, y.hu); }
+        else if (cy == 2) { l = enc_mul(x.hd, x.hu, y.ld, y.lu); h = enc_mul(x.ld, x.lu, y.hd, y.hu); }
+        else { l = enc_mul(x.hd, x.hu, y.ld, y.lu); h = enc_mul(x.hd, x.hu, y.hd, y.hu); }
+    } else if (cx == 2) {
+        if (cy == 1) { l = enc_mul(x.ld, x.lu, y.hd, y.hu); h = enc_mul(x.hd, x.hu, y.ld, y.lu); }
+        else if (cy == 2) { l = enc_mul(x.hd, x.hu, y.hd, y.hu); h = enc_mul(x.ld, x.lu, y.ld, y.lu); }
+        else { l = enc_mul(x.ld, x.lu, y.hd, y.hu); h = enc_mul(x.ld, x.lu, y.ld, y.lu); }
+    } else {
+        if (cy == 1) { l = enc_mul(x.ld, x.lu, y.hd, y.hu); h = enc_mul(x.hd, x.hu, y.hd, y.hu); }
+        else if (cy == 2) { l = enc_mul(x.hd, x.hu, y.ld, y.lu); h = enc_mul(x.ld, x.lu, y.ld, y.lu); }
+        else {
+            const float2 l1 = enc_mul(x.ld, x.lu, y.hd, y.hu), l2 = enc_mul(x.hd, x.hu, y.ld, y.lu);
+            const float2 h1 = enc_mul(x.ld, x.lu, y.ld, y.lu), h2 = enc_mul(x.hd, x.hu, y.hd, y.hu);
+            l = make_float2(fminf(l1.x, l2.x), fminf(l1.y, l2.y));
+            h = make_float2(fmaxf(h1.x, h2.x), fmaxf(h1.y, h2.y));
+        }
+    }
+    return {l.x, l.y, h.x, h.y};
+}
+
+// x^k (k >= 1) by the power rule of iv_pow: each FP64 chain p <- r64(p * v) is enclosed
+// by the down chain of the lower enclosure end and the up chain of the upper end.
+__device__ __forceinline__ shv sh_pow(shv x, int k, bool &poison) {
+    if (k == 1) return x;
+    if ((k & 1) == 0) {
+        if (x.ld >= 0.0f)
+            return {fchain_rd(x.ld, k), fchain_ru(x.lu, k), fchain_rd(x.hd, k), fchain_ru(x.hu, k)};
+        if (x.hu <= 0.0f)
+            return {fchain_rd(-x.hu, k), fchain_ru(-x.hd, k), fchain_rd(-x.lu, k), fchain_ru(-x.ld, k)};
+        if (x.lu < 0.0f && x.hd > 0.0f) {
+            const float md = fmaxf(-x.lu, x.hd), mu = fmaxf(-x.ld, x.hu);
+            return {0.0f, 0.0f, fchain_rd(md, k), fchain_ru(mu, k)};
+        }
+        poison = true;
+        return {0.f, 0.f, 0.f, 0.f};
+    }
+    shv r;
+    if (x.ld >= 0.0f) { r.ld = fchain_rd(x.ld, k); r.lu = fchain_ru(x.lu, k); }
+    else if (x.lu < 0.0f) { r.ld = -fchain_ru(-x.ld, k); r.lu = -fchain_rd(-x.lu, k); }
+    else { poison = true; return {0.f, 0.f, 0.f, 0.f}; }
+    if (x.hd >= 0.0f) { r.hd = fchain_rd(x.hd, k); r.hu = fchain_ru(x.hu, k); }
+    else if (x.hu < 0.0f) { r.hd = -fchain_ru(-x.hd, k); r.hu = -fchain_rd(-x.hu, k); }
+    else { poison = true; return {0.f, 0.f, 0.f, 0.f}; }
+    return r;
+}
+
 }  // namespace ivs

@@ -1,22 +1,24 @@
-// ivs_kernels.cu -- the per-box sweep over the device queue (sm_103a).
+// ivs_kernels.cu -- the per-box sweep over the device queue (sm_103a): control,
+// evaluation stages, and the sweep loop as one CUDA graph.
 //
-// Paper map: Definition 1-2 and Algorithm 2 (evaluation + exclusion of the 2^n children
-// of each parent), Section 2.3 / Algorithm 3 (Hansen-Sengupta sweep: Jacobian, Gauss-Jordan
-// preconditioner of Section 2.4, Algorithm 4 products, Gauss-Seidel of eq 21-22 with the
-// extended division of eq 10), Algorithm 1 (accept at the desired width or split again).
-// Every operation sequence matches the serial definition step for step (same fold orders,
-// same roundings), so the sorted result set is identical to the serial solver's.
+// Paper map: Definition 1-2 and Algorithm 2 (evaluation and exclusion of the 2^n children
+// of each parent); Algorithm 1 (the loop M_k -> M_{k+1} until the queue is empty).  The
+// Hansen-Sengupta stage and the accept / split step are in ivs_hs.cuh.  Every operation
+// sequence matches the serial definition step for step (same fold orders, same
+// roundings), so the sorted result set is identical to the serial solver's.
 #include <cuda_runtime.h>
 
 #include "ivs_internal.h"
 #include "ivs_interval.cuh"
 #include "ivs_kernels.cuh"
+#include "ivs_tab.cuh"
 
 namespace ivs {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kEvalMaxThreads = 256;
-constexpr int kEvalMaxWarps = kEvalMaxThreads / 32;
+constexpr int kEvalThreads = 256;
+constexpr int kEvalWarps = kEvalThreads / 32;
+constexpr int kEval64Threads = 128;
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
@@ -106,84 +108,75 @@ __global__ void k_loop_cond(SweepArgs a, cudaGraphConditionalHandle h) {
 }
 
 // ------------------------------------------------------------------------------------
-// evaluation: natural interval extension of every equation on each child box
+// evaluation of the children of each parent
 // ------------------------------------------------------------------------------------
 
-// FP64 F_i over child c of the warp's parent.  Coordinates: s_p[0][j] = lo_j,
-// s_p[1][j] = mid_j, s_p[2][j] = hi_j; child c has [lo, mid] or [mid, hi] in coordinate
-// j by bit j of c.  Returns false as soon as one F_i excludes 0.
-__device__ bool eval_keep64(const DevTables &tb, const DevSys &S, const double (*s_p)[kMaxVars],
-                            unsigned c) {
-    for (int i = 0; i < S.m; i++) {
-        const int p = S.f_poly + i;
-        const int t0 = tb.poly_term_off[p], t1 = tb.poly_term_off[p + 1];
-        ivd acc = {0.0, 0.0};
-        for (int t = t0; t < t1; t++) {
-            const ivd cf = {tb.term_clo[t], tb.term_chi[t]};
-            const int f0 = tb.term_fac_off[t], f1 = tb.term_fac_off[t + 1];
-            ivd v;
-            if (f0 == f1) {
-                v = cf;
-            } else {
-                unsigned fc = tb.fac[f0];
-                unsigned j = fc >> 4, up = (c >> j) & 1u;
-                ivd prod = iv_pow(ivd{s_p[up][j], s_p[up + 1][j]}, (int)(fc & 15u));
-                for (int f = f0 + 1; f < f1; f++) {
-                    fc = tb.fac[f];
-                    j = fc >> 4;
-                    up = (c >> j) & 1u;
-                    prod = iv_mul(prod, iv_pow(ivd{s_p[up][j], s_p[up + 1][j]}, (int)(fc & 15u)));
-                }
-                v = iv_mul(cf, prod);
-            }
-            acc = (t == t0) ? v : iv_add(acc, v);
-        }
-        if (d_pos(acc.lo) || d_neg(acc.hi)) return false;
+// Child c of the warp's parent: coordinate j is [lo_j, mid_j] when bit j of c is clear,
+// [mid_j, hi_j] when set.  p[0|1|2][j] = lo / mid / hi in FP64; f[0..3][j] = rd32(lo),
+// rd32(mid), ru32(mid), ru32(hi); e[0..5][j] = rd32 / ru32 of lo, mid, hi.
+struct ChildCoord64 {
+    const double (*p)[kMaxVars];
+    unsigned c;
+    __device__ __forceinline__ ivd operator()(unsigned j) const {
+        const unsigned up = (c >> j) & 1u;
+        return ivd{p[up][j], p[up + 1][j]};
     }
-    return true;
+};
+struct ChildCoord32 {
+    const float (*f)[kMaxVars];
+    unsigned c;
+    __device__ __forceinline__ ivf operator()(unsigned j) const {
+        const unsigned up = (c >> j) & 1u;
+        return ivf{f[up][j], f[up + 2][j]};
+    }
+};
+struct ChildCoordShadow {
+    const float (*e)[kMaxVars];
+    unsigned c;
+    __device__ __forceinline__ shv operator()(unsigned j) const {
+        const unsigned up = (c >> j) & 1u;
+        return shv{e[2 * up][j], e[2 * up + 1][j], e[2 * up + 2][j], e[2 * up + 3][j]};
+    }
+};
+// box held in shared memory, structure of arrays with the given stride
+struct BoxCoord {
+    const double *X;
+    int stride;
+    __device__ __forceinline__ ivd operator()(unsigned j) const {
+        return ivd{X[(2 * j) * stride], X[(2 * j + 1) * stride]};
+    }
+};
+
+__device__ __forceinline__ void push_surv(const SweepArgs &a, WaveCtl *ctl, int n, bool keep, Surv sv) {
+    const unsigned km = __ballot_sync(kFull, keep);
+    if (!km) return;
+    unsigned long long pos = 0;
+    if (lane_id() == 0) pos = atomicAdd((unsigned long long *)&ctl->surv_count[n], (unsigned long long)__popc(km));
+    pos = __shfl_sync(kFull, pos, 0);
+    if (keep) {
+        const unsigned long long k = pos + __popc(km & lanemask_lt());
+        if ((long long)k < a.surv_cap) a.surv[(size_t)n * a.surv_cap + k] = sv;
+        else ctl->error = 1;
+    }
 }
 
-// FP32 outward evaluation of the same operation sequence.  s_f[0][j] = rd32(lo_j),
-// s_f[1][j] = rd32(mid_j), s_f[2][j] = ru32(mid_j), s_f[3][j] = ru32(hi_j).
-__device__ bool eval_keep32(const DevTables &tb, const DevSys &S, const float (*s_f)[kMaxVars],
-                            unsigned c) {
-    for (int i = 0; i < S.m; i++) {
-        const int p = S.f_poly + i;
-        const int t0 = tb.poly_term_off[p], t1 = tb.poly_term_off[p + 1];
-        ivf acc = {0.0f, 0.0f};
-        for (int t = t0; t < t1; t++) {
-            const ivf cf = {tb.term_clo32[t], tb.term_chi32[t]};
-            const int f0 = tb.term_fac_off[t], f1 = tb.term_fac_off[t + 1];
-            ivf v;
-            if (f0 == f1) {
-                v = cf;
-            } else {
-                unsigned fc = tb.fac[f0];
-                unsigned j = fc >> 4, up = (c >> j) & 1u;
-                ivf prod = fv_pow(ivf{s_f[up][j], s_f[up + 2][j]}, (int)(fc & 15u));
-                for (int f = f0 + 1; f < f1; f++) {
-                    fc = tb.fac[f];
-                    j = fc >> 4;
-                    up = (c >> j) & 1u;
-                    prod = fv_mul(prod, fv_pow(ivf{s_f[up][j], s_f[up + 2][j]}, (int)(fc & 15u)));
-                }
-                v = fv_mul(cf, prod);
-            }
-            acc = (t == t0) ? v : fv_add(acc, v);
-        }
-        if (acc.lo > 0.0f || acc.hi < 0.0f) return false;
-    }
-    return true;
-}
-
-// One warp per parent (taken from a shared cursor), one lane per child.
-__global__ void __launch_bounds__(kEvalMaxThreads) k_eval(SweepArgs a) {
-    __shared__ double s_p[kEvalMaxWarps][3][kMaxVars];
-    __shared__ float s_f[kEvalMaxWarps][4][kMaxVars];
+// One warp per parent (taken from a shared cursor), one lane per child.  Three forms:
+// the FP32 shadow (decides what FP64 would decide with certainty; the undecided rest go
+// to k_eval64), the plain FP32 prefilter (its survivors go to k_eval64), or FP64 only.
+__global__ void __launch_bounds__(kEvalThreads) k_eval(SweepArgs a) {
+    extern __shared__ __align__(16) char s_blob[];
+    __shared__ double s_p[kEvalWarps][3][kMaxVars];
+    __shared__ float s_f[kEvalWarps][4][kMaxVars];
+    __shared__ float s_e[kEvalWarps][6][kMaxVars];
     const unsigned lane = lane_id();
     const int w = threadIdx.x >> 5;
     WaveCtl *ctl = a.ctl;
     const int64_t base = ctl->base, K = ctl->k;
+    if (a.single) {
+        const DevSys &S0 = a.tb.sys[0];
+        copy_blob(s_blob, a.tb.blobs + S0.blob_off, (uint32_t)S0.blob_bytes);
+        __syncthreads();
+    }
     for (;;) {
         int p = 0;
         if (lane == 0) p = atomicAdd(&ctl->cursor, 1);
@@ -193,6 +186,7 @@ __global__ void __launch_bounds__(kEvalMaxThreads) k_eval(SweepArgs a) {
         const int sys = a.q.sys[pi];
         const uint32_t meta = a.q.meta[pi];
         const DevSys S = a.tb.sys[sys];
+        const SysTab T = make_tab(a.single ? s_blob : a.tb.blobs + S.blob_off, S);
         const bool root = (meta & kRootFlag) != 0;
         const int depth = (int)(meta & kDepthMask) + (root ? 0 : 1);
         if (S.max_boxes > 0) {
@@ -210,40 +204,44 @@ __global__ void __launch_bounds__(kEvalMaxThreads) k_eval(SweepArgs a) {
             s_p[w][0][lane] = lo;
             s_p[w][1][lane] = mid;
             s_p[w][2][lane] = hi;
-            s_f[w][0][lane] = __double2float_rd(lo);
-            s_f[w][1][lane] = __double2float_rd(mid);
-            s_f[w][2][lane] = __double2float_ru(mid);
-            s_f[w][3][lane] = __double2float_ru(hi);
+            const float lod = __double2float_rd(lo), lou = __double2float_ru(lo);
+            const float mdd = __double2float_rd(mid), mdu = __double2float_ru(mid);
+            const float hid = __double2float_rd(hi), hiu = __double2float_ru(hi);
+            s_f[w][0][lane] = lod;
+            s_f[w][1][lane] = mdd;
+            s_f[w][2][lane] = mdu;
+            s_f[w][3][lane] = hiu;
+            s_e[w][0][lane] = lod;
+            s_e[w][1][lane] = lou;
+            s_e[w][2][lane] = mdd;
+            s_e[w][3][lane] = mdu;
+            s_e[w][4][lane] = hid;
+            s_e[w][5][lane] = hiu;
         }
         __syncwarp();
         const unsigned fan = root ? 1u : (1u << n);
-        unsigned cnt_pre = 0, cnt_ev = 0, cnt_64 = 0;
+        unsigned cnt_pre = 0, cnt_ev = 0, cnt_64 = 0, cnt_sh = 0;
         for (unsigned c0 = 0; c0 < fan; c0 += 32) {
             const unsigned c = c0 + lane;
             const bool active = c < fan;
             bool keep = false, cand = false;
             if (active) {
-                if (S.prefilter) {
-                    // FP32 stage; its survivors are evaluated in FP64 densely by k_eval64
-                    cand = eval_keep32(a.tb, S, s_f[w], c);
+                if (S.prefilter && S.shadow) {
+                    const int r = decide_shadow(T, S, ChildCoordShadow{s_e[w], c});
+                    keep = r == 1;
+                    cand = r == 2;
+                    cnt_pre += r == 0 ? 1u : 0u;
+                    cnt_sh += keep ? 1u : 0u;
+                } else if (S.prefilter) {
+                    cand = keep32(T, S, ChildCoord32{s_f[w], c});
                     cnt_pre += cand ? 0u : 1u;
                 } else {
                     cnt_64 += 1;
-                    keep = eval_keep64(a.tb, S, s_p[w], c);
+                    keep = keep64(T, S, ChildCoord64{s_p[w], c});
                     cnt_ev += keep ? 0u : 1u;
                 }
             }
-            const unsigned km = __ballot_sync(kFull, keep);
-            if (km) {
-                unsigned long long pos = 0;
-                if (lane == 0) pos = atomicAdd((unsigned long long *)&ctl->surv_count[n], (unsigned long long)__popc(km));
-                pos = __shfl_sync(kFull, pos, 0);
-                if (keep) {
-                    const unsigned long long k = pos + __popc(km & lanemask_lt());
-                    if ((long long)k < a.surv_cap) a.surv[(size_t)n * a.surv_cap + k] = Surv{(uint32_t)pi, c};
-                    else ctl->error = 1;
-                }
-            }
+            push_surv(a, ctl, n, keep, Surv{(uint32_t)pi, c});
             const unsigned cm = __ballot_sync(kFull, cand);
             if (cm) {
                 unsigned long long pos = 0;
@@ -259,59 +257,34 @@ __global__ void __launch_bounds__(kEvalMaxThreads) k_eval(SweepArgs a) {
         cnt_pre = __reduce_add_sync(kFull, cnt_pre);
         cnt_ev = __reduce_add_sync(kFull, cnt_ev);
         cnt_64 = __reduce_add_sync(kFull, cnt_64);
+        cnt_sh = __reduce_add_sync(kFull, cnt_sh);
         if (lane == 0) {
             atomicAdd(stat_ptr(a, sys, ST_BOXES), (unsigned long long)fan);
             if (cnt_pre) atomicAdd(stat_ptr(a, sys, ST_EXCL_PREFILTER), (unsigned long long)cnt_pre);
             if (cnt_ev) atomicAdd(stat_ptr(a, sys, ST_EXCL_EVAL), (unsigned long long)cnt_ev);
             if (cnt_64) atomicAdd(stat_ptr(a, sys, ST_EVAL64), (unsigned long long)cnt_64);
+            if (cnt_sh) atomicAdd(stat_ptr(a, sys, ST_KEEP_SHADOW), (unsigned long long)cnt_sh);
             atomicMax(stat_ptr(a, sys, ST_MAX_DEPTH), (unsigned long long)depth);
         }
         __syncwarp();
     }
 }
 
-// ------------------------------------------------------------------------------------
-// FP64 evaluation of the FP32 survivors, one thread per candidate (dense)
-// ------------------------------------------------------------------------------------
-
-constexpr int kEval64Threads = 128;
-
-// F_i over a box held in per-thread shared memory (runtime variable indices)
-__device__ bool eval_keep64_box(const DevTables &tb, const DevSys &S, const double *X, int T) {
-    for (int i = 0; i < S.m; i++) {
-        const int p = S.f_poly + i;
-        const int t0 = tb.poly_term_off[p], t1 = tb.poly_term_off[p + 1];
-        ivd acc = {0.0, 0.0};
-        for (int t = t0; t < t1; t++) {
-            const ivd cf = {tb.term_clo[t], tb.term_chi[t]};
-            const int f0 = tb.term_fac_off[t], f1 = tb.term_fac_off[t + 1];
-            ivd v;
-            if (f0 == f1) {
-                v = cf;
-            } else {
-                unsigned fc = tb.fac[f0];
-                unsigned j = fc >> 4;
-                ivd prod = iv_pow(ivd{X[(2 * j) * T], X[(2 * j + 1) * T]}, (int)(fc & 15u));
-                for (int f = f0 + 1; f < f1; f++) {
-                    fc = tb.fac[f];
-                    j = fc >> 4;
-                    prod = iv_mul(prod, iv_pow(ivd{X[(2 * j) * T], X[(2 * j + 1) * T]}, (int)(fc & 15u)));
-                }
-                v = iv_mul(cf, prod);
-            }
-            acc = (t == t0) ? v : iv_add(acc, v);
-        }
-        if (d_pos(acc.lo) || d_neg(acc.hi)) return false;
-    }
-    return true;
-}
-
+// FP64 evaluation of the candidates (undecided by the FP32 stage), one thread each,
+// 32 per warp from an atomic cursor so the work is dense and spread over all SMs.
 __global__ void __launch_bounds__(kEval64Threads) k_eval64(SweepArgs a) {
+    extern __shared__ __align__(16) char s_blob[];
     __shared__ double sX[2 * kMaxVars * kEval64Threads];
     const int T = blockDim.x, tid = threadIdx.x;
     double *X = sX + tid;
     WaveCtl *ctl = a.ctl;
     const int64_t count = ctl->cand_count;
+    if (count == 0) return;
+    if (a.single) {
+        const DevSys &S0 = a.tb.sys[0];
+        copy_blob(s_blob, a.tb.blobs + S0.blob_off, (uint32_t)S0.blob_bytes);
+        __syncthreads();
+    }
     const unsigned lane = lane_id();
     for (;;) {
         unsigned long long base = 0;
@@ -328,30 +301,20 @@ __global__ void __launch_bounds__(kEval64Threads) k_eval64(SweepArgs a) {
             const int64_t pi = sv.parent;
             sys = a.q.sys[pi];
             const DevSys S = a.tb.sys[sys];
+            const SysTab Tb = make_tab(a.single ? s_blob : a.tb.blobs + S.blob_off, S);
             n = S.n;
             for (int j = 0; j < n; j++) {
                 const bool up = (sv.child >> j) & 1u;
                 X[(2 * j) * T] = up ? a.q.mid[j * a.q.cap + pi] : a.q.lo[j * a.q.cap + pi];
                 X[(2 * j + 1) * T] = up ? a.q.hi[j * a.q.cap + pi] : a.q.mid[j * a.q.cap + pi];
             }
-            keep = eval_keep64_box(a.tb, S, X, T);
+            keep = keep64(Tb, S, BoxCoord{X, T});
         }
-        // survivors into the list of their dimension; counters per system
         const int sys0 = __shfl_sync(kFull, sys, 0);
         const int n0 = __shfl_sync(kFull, n, 0);
         const bool uniform = __all_sync(kFull, !active || (sys == sys0 && n == n0));
         if (uniform) {
-            const unsigned km = __ballot_sync(kFull, keep);
-            if (km) {
-                unsigned long long pos = 0;
-                if (lane == 0) pos = atomicAdd((unsigned long long *)&ctl->surv_count[n0], (unsigned long long)__popc(km));
-                pos = __shfl_sync(kFull, pos, 0);
-                if (keep) {
-                    const unsigned long long k = pos + __popc(km & lanemask_lt());
-                    if ((long long)k < a.surv_cap) a.surv[(size_t)n0 * a.surv_cap + k] = sv;
-                    else ctl->error = 1;
-                }
-            }
+            push_surv(a, ctl, n0, keep, sv);
             const unsigned na = __popc(__ballot_sync(kFull, active));
             const unsigned nk = __popc(__ballot_sync(kFull, keep));
             if (lane == 0) {
@@ -396,15 +359,26 @@ static cudaError_t launch_hs(const SweepArgs &a, int n, int num_sms, cudaStream_
     }
 }
 
+cudaError_t configure_eval_kernels(int blob_smem) {
+    if (blob_smem > 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, blob_smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_eval64, cudaFuncAttributeMaxDynamicSharedMemorySize, blob_smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_sweep(const SweepArgs &a, const int *hs_dims, int n_hs_dims, int eval_blocks,
                          int eval_threads, int num_sms, cudaStream_t st, cudaEvent_t *ev) {
     // ev (optional): n_hs_dims + 5 events recorded between the stages
+    const size_t blob = a.single ? (size_t)a.blob_smem : 0;
     if (ev) cudaEventRecord(ev[0], st);
     k_wave_begin<<<1, 32, 0, st>>>(a);
     if (ev) cudaEventRecord(ev[1], st);
-    k_eval<<<eval_blocks, eval_threads, 0, st>>>(a);
+    k_eval<<<eval_blocks, eval_threads, blob, st>>>(a);
     if (ev) cudaEventRecord(ev[2], st);
-    k_eval64<<<num_sms * 8, kEval64Threads, 0, st>>>(a);
+    k_eval64<<<num_sms * 4, kEval64Threads, blob, st>>>(a);
     if (ev) cudaEventRecord(ev[3], st);
     for (int q = 0; q < n_hs_dims; q++) {
         cudaError_t e = launch_hs(a, hs_dims[q], num_sms, st);

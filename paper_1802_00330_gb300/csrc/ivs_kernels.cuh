@@ -30,8 +30,12 @@ struct SweepArgs {
     int64_t wave_children;       // children a sweep may evaluate
     int32_t max_fan_shift;       // max n over the plan's systems
     int32_t n_sys;
+    int32_t single;              // 1: one system; kernels cache its blob in shared memory
+    int32_t blob_smem;           // bytes of that blob
 };
 
+// sets the dynamic shared memory limit of the evaluation kernels (blob cache)
+cudaError_t configure_eval_kernels(int blob_smem);
 // kernels per sweep: 4 + n_hs_dims; ev (nullable) receives n_hs_dims + 4 stage events
 cudaError_t launch_sweep(const SweepArgs &a, const int *hs_dims, int n_hs_dims, int eval_blocks,
                          int eval_threads, int num_sms, cudaStream_t st, cudaEvent_t *ev);

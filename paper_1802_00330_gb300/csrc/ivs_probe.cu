@@ -11,7 +11,8 @@ namespace ivs {
 constexpr int kProbeIters = 4096;
 constexpr int kProbeChains = 8;
 
-__global__ void k_probe_fp64(double seed, double *sink) {
+__global__ void k_probe_fp64(double seed, double *sink, int active_lanes) {
+    if ((int)(threadIdx.x & 31u) >= active_lanes) return;
     double x[kProbeChains];
 #pragma unroll
     for (int c = 0; c < kProbeChains; c++) x[c] = seed + c * 1e-3 + threadIdx.x * 1e-9;
@@ -51,14 +52,16 @@ cudaError_t run_probe(int kind, int num_sms, double *ops, float *ms) {
     const int threads = 256, blocks = num_sms * 8;
     for (int rep = 0; rep < 3; rep++) {   // first launches warm up clocks and caches
         cudaEventRecord(a);
-        if (kind == 0) k_probe_fp64<<<blocks, threads>>>(1.0, (double *)sink);
+        if (kind == 0) k_probe_fp64<<<blocks, threads>>>(1.0, (double *)sink, 32);
+        else if (kind >= 2) k_probe_fp64<<<blocks, threads>>>(1.0, (double *)sink, kind == 2 ? 8 : 1);
         else k_probe_fp32<<<blocks, threads>>>(1.0f, (float *)sink);
         cudaEventRecord(b);
     }
     e = cudaEventSynchronize(b);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
-    *ops = (double)blocks * threads * kProbeIters * kProbeChains * 2.0;
+    const int lanes = kind == 2 ? 8 : kind == 3 ? 1 : 32;
+    *ops = (double)blocks * (threads / 32) * lanes * kProbeIters * kProbeChains * 2.0;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaFree(sink);

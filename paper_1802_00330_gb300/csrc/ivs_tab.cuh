@@ -1,0 +1,181 @@
+// ivs_tab.cuh -- a compiled system's term table and the natural-form evaluators.
+//
+// Each system is compiled on the host into one contiguous blob (layout below) holding
+// its polynomials: the m equations F_i, then (when m == n) the m*n Jacobian entries J_ij.
+// A polynomial is a range of terms; a term is a coefficient interval and a list of
+// factors (var << 4 | exponent, exponent >= 1) in increasing variable order.  Kernels
+// read the blob from global memory or copy it once per block into shared memory.
+//
+// Evaluation follows Definition 1 with the operation order fixed once for every
+// implementation: a term folds its factor powers left in variable order, then the
+// coefficient interval multiplies the product; a polynomial folds its terms left in
+// input order.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ivs_internal.h"
+#include "ivs_interval.cuh"
+
+namespace ivs {
+
+// byte layout of a system blob with T terms, P polynomials and F factors
+struct BlobLayout {
+    uint32_t cs, clo, chi, clo32, chi32, poly_off, tinfo, fac, bytes;
+};
+__host__ __device__ inline BlobLayout blob_layout(int T, int P, int F) {
+    BlobLayout L;
+    uint32_t o = 0;
+    L.cs = o;        o += 16u * T;
+    L.clo = o;       o += 8u * T;
+    L.chi = o;       o += 8u * T;
+    L.clo32 = o;     o += 4u * T;
+    L.chi32 = o;     o += 4u * T;
+    L.poly_off = o;  o += 4u * (P + 1);
+    L.tinfo = o;     o += 4u * T;
+    L.fac = o;       o += (uint32_t)F;
+    L.bytes = (o + 15u) & ~15u;
+    return L;
+}
+
+struct SysTab {
+    const float4 *cs;        // {rd32(c_lo), ru32(c_lo), rd32(c_hi), ru32(c_hi)}
+    const double *clo, *chi; // coefficient interval
+    const float *clo32, *chi32;
+    const int32_t *poly_off; // [P + 1] term ranges
+    const uint32_t *tinfo;   // factor start << 5 | factor count
+    const uint8_t *fac;
+};
+
+__device__ __forceinline__ SysTab make_tab(const char *blob, const DevSys &S) {
+    const BlobLayout L = blob_layout(S.n_terms, S.n_polys, S.n_facs);
+    SysTab t;
+    t.cs = reinterpret_cast<const float4 *>(blob + L.cs);
+    t.clo = reinterpret_cast<const double *>(blob + L.clo);
+    t.chi = reinterpret_cast<const double *>(blob + L.chi);
+    t.clo32 = reinterpret_cast<const float *>(blob + L.clo32);
+    t.chi32 = reinterpret_cast<const float *>(blob + L.chi32);
+    t.poly_off = reinterpret_cast<const int32_t *>(blob + L.poly_off);
+    t.tinfo = reinterpret_cast<const uint32_t *>(blob + L.tinfo);
+    t.fac = reinterpret_cast<const uint8_t *>(blob + L.fac);
+    return t;
+}
+
+// cooperative copy of a blob (bytes a multiple of 16) into shared memory
+__device__ __forceinline__ void copy_blob(char *dst, const char *src, uint32_t bytes) {
+    const int4 *s = reinterpret_cast<const int4 *>(src);
+    int4 *d = reinterpret_cast<int4 *>(dst);
+    for (uint32_t i = threadIdx.x; i < bytes / 16u; i += blockDim.x) d[i] = s[i];
+}
+
+// ---- evaluators over a coordinate accessor x(j) ----------------------------------------
+
+template <class Coord>
+__device__ __forceinline__ ivd poly64(const SysTab &T, int p, const Coord &x) {
+    const int t0 = T.poly_off[p], t1 = T.poly_off[p + 1];
+    ivd acc = {0.0, 0.0};
+    for (int t = t0; t < t1; t++) {
+        const ivd cf = {T.clo[t], T.chi[t]};
+        const uint32_t info = T.tinfo[t];
+        const int nf = (int)(info & 31u), f0 = (int)(info >> 5);
+        ivd v;
+        if (nf == 0) {
+            v = cf;
+        } else {
+            unsigned fc = T.fac[f0];
+            ivd prod = iv_pow(x(fc >> 4), (int)(fc & 15u));
+            for (int f = 1; f < nf; f++) {
+                fc = T.fac[f0 + f];
+                prod = iv_mul(prod, iv_pow(x(fc >> 4), (int)(fc & 15u)));
+            }
+            v = iv_mul(cf, prod);
+        }
+        acc = (t == t0) ? v : iv_add(acc, v);
+    }
+    return acc;
+}
+
+template <class Coord>
+__device__ __forceinline__ ivf poly32(const SysTab &T, int p, const Coord &x) {
+    const int t0 = T.poly_off[p], t1 = T.poly_off[p + 1];
+    ivf acc = {0.0f, 0.0f};
+    for (int t = t0; t < t1; t++) {
+        const ivf cf = {T.clo32[t], T.chi32[t]};
+        const uint32_t info = T.tinfo[t];
+        const int nf = (int)(info & 31u), f0 = (int)(info >> 5);
+        ivf v;
+        if (nf == 0) {
+            v = cf;
+        } else {
+            unsigned fc = T.fac[f0];
+            ivf prod = fv_pow(x(fc >> 4), (int)(fc & 15u));
+            for (int f = 1; f < nf; f++) {
+                fc = T.fac[f0 + f];
+                prod = fv_mul(prod, fv_pow(x(fc >> 4), (int)(fc & 15u)));
+            }
+            v = fv_mul(cf, prod);
+        }
+        acc = (t == t0) ? v : fv_add(acc, v);
+    }
+    return acc;
+}
+
+template <class Coord>
+__device__ __forceinline__ shv poly_shadow(const SysTab &T, int p, const Coord &x, bool &poison) {
+    const int t0 = T.poly_off[p], t1 = T.poly_off[p + 1];
+    shv acc = {0.f, 0.f, 0.f, 0.f};
+    for (int t = t0; t < t1; t++) {
+        const float4 ce = T.cs[t];
+        const shv cf = {ce.x, ce.y, ce.z, ce.w};
+        const uint32_t info = T.tinfo[t];
+        const int nf = (int)(info & 31u), f0 = (int)(info >> 5);
+        shv v;
+        if (nf == 0) {
+            v = cf;
+        } else {
+            unsigned fc = T.fac[f0];
+            shv prod = sh_pow(x(fc >> 4), (int)(fc & 15u), poison);
+            for (int f = 1; f < nf; f++) {
+                fc = T.fac[f0 + f];
+                prod = sh_mul(prod, sh_pow(x(fc >> 4), (int)(fc & 15u), poison), poison);
+            }
+            v = sh_mul(cf, prod, poison);
+        }
+        acc = (t == t0) ? v : sh_add(acc, v);
+    }
+    return acc;
+}
+
+// Definition 2 in FP64: false as soon as one F_i excludes 0 (NaN ends never exclude)
+template <class Coord>
+__device__ __forceinline__ bool keep64(const SysTab &T, const DevSys &S, const Coord &x) {
+    for (int i = 0; i < S.m; i++) {
+        const ivd F = poly64(T, S.f_poly + i, x);
+        if (d_pos(F.lo) || d_neg(F.hi)) return false;
+    }
+    return true;
+}
+
+template <class Coord>
+__device__ __forceinline__ bool keep32(const SysTab &T, const DevSys &S, const Coord &x) {
+    for (int i = 0; i < S.m; i++) {
+        const ivf F = poly32(T, S.f_poly + i, x);
+        if (F.lo > 0.0f || F.hi < 0.0f) return false;
+    }
+    return true;
+}
+
+// FP32 shadow decision: 0 = FP64 would exclude, 1 = FP64 would keep, 2 = undecided
+template <class Coord>
+__device__ __forceinline__ int decide_shadow(const SysTab &T, const DevSys &S, const Coord &x) {
+    bool undecided = false;
+    for (int i = 0; i < S.m; i++) {
+        bool poison = false;
+        const shv F = poly_shadow(T, S.f_poly + i, x, poison);
+        if (poison) { undecided = true; continue; }
+        if (F.ld > 0.0f || F.hu < 0.0f) return 0;        // lo64 > 0 or hi64 < 0
+        if (!(F.lu <= 0.0f && F.hd >= 0.0f)) undecided = true;
+    }
+    return undecided ? 2 : 1;
+}
+
+}  // namespace ivs
