@@ -184,6 +184,41 @@ int32_t ivs_plan_kernel_times(ivs_plan *p, ivs_kernel_time *out, int32_t max);
  * or one multiply = one operation) and the kernel time. */
 int ivs_probe_rate(int32_t kind, int32_t device, double *ops_per_s, double *ms);
 
+/* ---- allocation-free solve ------------------------------------------------------ */
+/* No counterpart in the paper: an entry point for callers that cannot allocate.  Code
+ * that runs while a CUDA stream is being captured into a graph, processes whose device
+ * memory belongs to a pool they must not bypass, and allocation-free real-time loops
+ * cannot call cudaMalloc.  ivs_solve_noalloc solves one system like ivs_solve but
+ * allocates nothing: every byte of device scratch comes from one fixed file-scope
+ * __device__ array of IVS_NOALLOC_SCRATCH_BYTES inside the library (present on every
+ * GPU that loads the library, until the process exits), host work uses static buffers
+ * and the stack, and it calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Limits of the fixed buffers: n_vars <= 12, a compiled term table (equations plus
+ * Jacobian) of at most 48 KiB / 2048 terms, and at most 16384 boxes held as results.
+ * Larger systems are rejected with IVS_ERR_INVALID and a message in errbuf; a solve
+ * whose queue outgrows the buffer returns IVS_ERR_NOMEM, and one with more accepted
+ * boxes than out_cap or 16384 returns IVS_ERR_BUDGET with the first ones.
+ *
+ * Inputs (host pointers) as for ivs_solve.  stream: a cudaStream_t or NULL (the legacy
+ * default stream); the call returns after the solve.  Outputs (host memory owned by the
+ * caller): out_lo / out_hi receive up to out_cap boxes of n_vars doubles, row-major and
+ * sorted as in ivs_result_boxes; out_flags (may be NULL) their IVS_BOX_* flags;
+ * *out_count the number written; stats (may be NULL) the counters; errbuf (may be NULL)
+ * a message of at most errbuf_len bytes.  Returns an IVS_* status.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  Every
+ * call shares the one array and it keeps the previous call's contents (the call clears
+ * what must start at zero): calls that overlap on the GPU -- from several host threads
+ * on different streams, or on one device from several processes' views of it -- race.
+ * Host threads are serialised by a lock inside the library. */
+#define IVS_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+int ivs_solve_noalloc(const ivs_system *sys, const double *box_lo, const double *box_hi,
+                      const ivs_options *opt, void *stream, double *out_lo, double *out_hi,
+                      int32_t *out_flags, int64_t out_cap, int64_t *out_count, ivs_stats *stats,
+                      char *errbuf, int32_t errbuf_len);
+
 const char *ivs_status_str(int status);
 const char *ivs_last_error(void);   /* thread-local text of the last error           */
 

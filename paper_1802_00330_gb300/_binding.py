@@ -76,6 +76,9 @@ SIGNATURES = {
     "ivs_plan_destroy": (None, [_VP]),
     "ivs_plan_kernel_times": (C.c_int32, [_VP, _VP, C.c_int32]),
     "ivs_probe_rate": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "ivs_solve_noalloc": (C.c_int, [C.POINTER(ivs_system), _VP, _VP, C.POINTER(ivs_options), _VP, _VP, _VP,
+                                    _VP, C.c_int64, C.POINTER(C.c_int64), C.POINTER(ivs_stats), C.c_char_p,
+                                    C.c_int32]),
     "ivs_status_str": (C.c_char_p, [C.c_int]),
     "ivs_last_error": (C.c_char_p, []),
 }
