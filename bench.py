@@ -86,6 +86,19 @@ def hs_ops(s):
             + 4 * n * n - 2 * n + n * (6 * (n - 1) + 4) + 2 * n)
 
 
+# ---- multi-rank aggregation ----------------------------------------------------------
+def reduce_over_ranks(t_dev, boxes, device="cpu"):
+    """Whole-job numbers over the ranks of the default process group: the slowest
+    rank's time (max) and the total boxes (sum).  Replicas share nothing else."""
+    import torch
+    import torch.distributed as td
+    tt = torch.tensor([float(t_dev)], dtype=torch.float64, device=device)
+    bb = torch.tensor([float(boxes)], dtype=torch.float64, device=device)
+    td.all_reduce(tt, op=td.ReduceOp.MAX)
+    td.all_reduce(bb, op=td.ReduceOp.SUM)
+    return float(tt.item()), float(bb.item())
+
+
 # ---- clocks --------------------------------------------------------------------------
 class ClockSampler:
     def __init__(self, index=0):
@@ -185,7 +198,13 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
         td.init_process_group("nccl")
 
     stream = torch.cuda.Stream()
-    plan = B.Plan(systems, stream=stream, wave_children=args.wave_children)       # graph path
+    tuned = None
+    if args.workload == "batched" and not args.wave_children:
+        # batching form: the autotuner picks the sweep size and evaluation grid (outside timing)
+        tuned = B.autotune(systems[: min(len(systems), 256)], trial_boxes=100_000)
+        args.wave_children = int(tuned["wave_children"])
+    plan = B.Plan(systems, stream=stream, wave_children=args.wave_children,
+                  eval_blocks=(tuned or {}).get("eval_blocks", 0))       # graph path
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
 
     def one_step():
@@ -224,12 +243,7 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
     ck = clocks.stop()
     t_dev = float(np.sum(step_t))
     if dist:
-        tt = torch.tensor([t_dev], device="cuda")
-        td.all_reduce(tt, op=td.ReduceOp.MAX)
-        t_dev = float(tt.item())
-        bb = torch.tensor([boxes], device="cuda", dtype=torch.float64)
-        td.all_reduce(bb)
-        boxes_all = float(bb.item())
+        t_dev, boxes_all = reduce_over_ranks(t_dev, boxes, device="cuda")
     else:
         boxes_all = boxes
     value = boxes_all / t_dev
@@ -238,7 +252,9 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
     if args.only_timed:
         if rank == 0:
             print(json.dumps({"metric": "boxes/sec", "value": boxes_all / t_dev, "unit": "boxes/s",
-                              "ms_per_step": 1e3 * t_dev / args.steps, "only_timed": True}), flush=True)
+                              "systems_per_s": world * len(systems) * args.steps / t_dev,
+                              "ms_per_step": 1e3 * t_dev / args.steps, "only_timed": True, "autotuned": tuned,
+                              "config": {"workload": desc}}), flush=True)
         plan.close()
         return None
     # parity guard: the timed solve's result equals the warm-up solve's
@@ -365,6 +381,69 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
     return out
 
 
+def run_served(args, rank, world, local_rank):
+    """Continuous batching: Poisson arrivals of served-config systems, submitted at their
+    arrival times to one server; latency = result ready - arrival."""
+    import threading as th
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_1802_00330_gb300 import _binding as B
+    times, systems = synth.config_served(duration_s=args.served_seconds, rate=args.served_rate)
+    sv = B.Server(workspace_bytes=args.served_workspace << 30, max_slots=1024, wave_children=1 << 22)
+    # warm-up: a few small requests
+    for s in systems[:3]:
+        sv.wait(sv.submit(s, time_budget_s=args.served_budget), timeout_s=60.0)
+    tickets = [None] * len(systems)
+    arrival = [0.0] * len(systems)
+    done_t = [None] * len(systems)
+    results = [None] * len(systems)
+    t0 = time.perf_counter() + 0.05
+
+    def submitter():
+        for k, (ta, s) in enumerate(zip(times, systems)):
+            delay = t0 + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            arrival[k] = t0 + ta
+            tickets[k] = sv.submit(s, time_budget_s=args.served_budget)
+
+    def collector():
+        for k in range(len(systems)):
+            while tickets[k] is None:
+                time.sleep(0.0005)
+            r = sv.wait(tickets[k], timeout_s=0.0)
+            done_t[k] = time.perf_counter()
+            results[k] = r
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    a = th.Thread(target=submitter)
+    b = th.Thread(target=collector)
+    a.start(); b.start(); a.join(); b.join()
+    wall = time.perf_counter() - t0
+    ck = clocks.stop()
+    lat = np.array([(done_t[k] - arrival[k]) * 1e3 for k in range(len(systems))])
+    status = np.array([r["status"] for r in results])
+    boxes = sum(r["stats"]["boxes"] for r in results)
+    st = sv.stats()
+    sv.close()
+    ok = status == 0
+    line = {"metric": "served systems/sec (continuous batching)", "value": len(systems) / wall, "unit": "systems/s",
+            "n_gpus": world, "higher_is_better": True, "dtype": "f64 (f32 prefilter)", "data": "synthetic",
+            "config": {"workload": f"served: Poisson {args.served_rate} req/s for {args.served_seconds} s, n~U{{3..12}}, "
+                                   "deg<=4, 6-14 monomials/eq, planted roots, box [-2,2]^n, tol 1e-6",
+                       "time_budget_s_per_request": args.served_budget},
+            "offered_rate": args.served_rate, "requests": len(systems), "wall_s": wall,
+            "completed_ok": int(ok.sum()), "timed_out": int((status == 4).sum()),
+            "status_counts": {int(k): int(v) for k, v in zip(*np.unique(status, return_counts=True))},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "p50_ok": float(np.percentile(lat[ok], 50)) if ok.any() else None,
+                           "p99_ok": float(np.percentile(lat[ok], 99)) if ok.any() else None},
+            "boxes_per_s": boxes / wall, "server": st, "clocks": ck}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,13 +455,26 @@ def main():
     ap.add_argument("--cpu-boxes", type=int, default=600_000)
     ap.add_argument("--ref-boxes", type=int, default=200_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--served-rate", type=float, default=2000.0)
+    ap.add_argument("--served-seconds", type=float, default=2.0)
+    ap.add_argument("--served-budget", type=float, default=2.0)
+    ap.add_argument("--served-workspace", type=int, default=16, help="GiB")
+    ap.add_argument("--batched-count", type=int, default=4096)
     ap.add_argument("--only-timed", action="store_true",
                     help="time the device-resident solve only (for profiler runs)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
-    systems, desc = workload(args.workload)
+    if args.workload == "served" and args.impl != "reference":
+        run_served(args, rank, world, local_rank)
+        return
+    if args.workload == "batched":
+        systems, desc = synth.config_batched(count=args.batched_count), (
+            f"batched: {args.batched_count} seeded systems, n~U{{2..8}}, 4-10 monomials/eq, deg<=3, "
+            "int coef [-5,5], planted roots, box [-4,4]^n, tol 1e-6")
+    else:
+        systems, desc = workload(args.workload)
     if args.impl == "reference":
         run_reference(args, systems, desc, rank, world)
         return

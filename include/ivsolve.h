@@ -101,6 +101,8 @@ typedef struct ivs_stats {
     int64_t launches;           /* kernels the solve launched                          */
     int64_t eval64_boxes;       /* boxes that ran the FP64 evaluation                  */
     int64_t kept_shadow;        /* boxes the FP32 shadow proved FP64 would keep        */
+    double queue_ms;            /* served requests: submit -> admission                */
+    double solve_ms;            /* served requests: admission -> result ready          */
 } ivs_stats;
 
 typedef struct ivs_result ivs_result;
@@ -166,6 +168,16 @@ int ivs_plan_result(ivs_plan *p, int32_t s, ivs_result **out);
 int ivs_plan_stats(ivs_plan *p, ivs_stats *st);   /* totals over all systems, last run */
 void ivs_plan_destroy(ivs_plan *p);
 
+/* Autotuner of the batching form (no paper counterpart): for the given systems it runs
+ * short trial solves (each system capped at trial_boxes processed boxes) with every
+ * combination of wave_children in {2^20, 2^22, 2^24} and evaluation grids of {4, 8, 16}
+ * blocks per SM, and writes the configuration with the highest boxes/s to *best (its
+ * other fields zero) and that rate to *best_rate.  The choices only schedule work:
+ * results do not depend on them. */
+int ivs_autotune(int32_t n_sys, const ivs_system *systems, const double *const *box_lo,
+                 const double *const *box_hi, const ivs_options *opts, int32_t opts_stride,
+                 int64_t trial_boxes, ivs_plan_cfg *best, double *best_rate);
+
 /* Per-kernel-class device time of the last run of a plan created with cfg.profile = 1
  * (CUDA events on the plan's stream around each launch).  Writes up to max entries and
  * returns how many classes exist.  Class names: "eval", "hs_n<k>", "control". */
@@ -183,6 +195,53 @@ int32_t ivs_plan_kernel_times(ivs_plan *p, ivs_kernel_time *out, int32_t max);
  * idle lanes cost FP64 issue time).  Writes the rate in operations per second (one add
  * or one multiply = one operation) and the kernel time. */
 int ivs_probe_rate(int32_t kind, int32_t device, double *ops_per_s, double *ms);
+
+/* ---- serving: continuous batching over one shared device queue ------------------- */
+/* A server keeps one device-resident queue for every system in flight.  Requests that
+ * arrive while others run are admitted between sweeps (one sweep = Algorithm 2's
+ * evaluation of every child of the popped parents, then Algorithm 3 and the accept /
+ * split step) as soon as a slot and queue memory are free: a request reserves
+ * 64 * 2^n queue entries (reserve_factor scales it), and admission stops while the
+ * reservations of the systems in flight would exceed half of the queue.  Their sweeps
+ * share kernels with the systems already running.  A system is solved when none of its
+ * boxes remain in the queue; its result (the same as ivs_solve's, bit for bit: each box's
+ * fate depends only on the box) is then ready for ivs_server_poll / ivs_server_wait.
+ * Submissions and polls may come from any host thread; one worker thread drives the GPU. */
+typedef struct ivs_server ivs_server;
+typedef struct ivs_server_cfg {
+    size_t workspace_bytes;   /* device memory for the shared queue (0 = 4 GiB); sweep
+                                 staging and the result regions are allocated on top     */
+    int64_t wave_children;    /* children per sweep (0 = 2^22)                            */
+    int64_t results_per_slot; /* result capacity of one request (0 = 16384)               */
+    int32_t max_slots;        /* systems in flight at once (0 = 1024)                     */
+    int32_t max_vars;         /* largest n accepted (0 = 12, at most 16)                  */
+    int32_t sweeps_per_step;  /* sweeps between admissions / completion checks (0 = 2)    */
+    int32_t device;           /* CUDA device ordinal                                      */
+    double reserve_factor;    /* scales the per-request queue reservation (0 = 1)         */
+} ivs_server_cfg;
+
+typedef struct ivs_server_stats {
+    int64_t submitted, admitted, completed, in_flight, waiting;
+    int64_t steps, sweeps, boxes;
+    double busy_s;            /* worker time with systems in flight                       */
+    char last_error[160];     /* the worker's last error text ("" if none)                */
+} ivs_server_stats;
+
+void ivs_server_cfg_default(ivs_server_cfg *cfg);
+int ivs_server_create(const ivs_server_cfg *cfg, ivs_server **out);
+/* Copies the system, box and options (validated as for ivs_solve; n_vars <= max_vars)
+ * and queues the request; *ticket identifies it. */
+int ivs_server_submit(ivs_server *sv, const ivs_system *sys, const double *box_lo, const double *box_hi,
+                      const ivs_options *opt, uint64_t *ticket);
+/* IVS_OK with *out = NULL while pending; IVS_OK with *out = the result once done (the
+ * caller then owns it: ivs_result_free); IVS_ERR_INVALID for an unknown ticket.  The
+ * result's stats carry queue_ms (submit -> admission) and solve_ms (admission -> done). */
+int ivs_server_poll(ivs_server *sv, uint64_t ticket, ivs_result **out);
+/* Like poll but blocks up to timeout_s seconds (<= 0: no limit). */
+int ivs_server_wait(ivs_server *sv, uint64_t ticket, double timeout_s, ivs_result **out);
+int ivs_server_get_stats(ivs_server *sv, ivs_server_stats *st);
+/* Stops the worker (requests not finished are dropped) and frees everything. */
+void ivs_server_destroy(ivs_server *sv);
 
 /* ---- allocation-free solve ------------------------------------------------------ */
 /* No counterpart in the paper: an entry point for callers that cannot allocate.  Code

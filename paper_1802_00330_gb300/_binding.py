@@ -40,13 +40,25 @@ class ivs_stats(C.Structure):
                 ("hs_singular", C.c_int64), ("accepted", C.c_int64), ("unsplittable", C.c_int64),
                 ("split", C.c_int64), ("max_depth_seen", C.c_int32), ("waves", C.c_int32),
                 ("device_ms", C.c_double), ("launches", C.c_int64), ("eval64_boxes", C.c_int64),
-                ("kept_shadow", C.c_int64)]
+                ("kept_shadow", C.c_int64), ("queue_ms", C.c_double), ("solve_ms", C.c_double)]
 
 
 class ivs_plan_cfg(C.Structure):
     _fields_ = [("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t), ("stream", C.c_void_p),
                 ("wave_children", C.c_int64), ("eval_blocks", C.c_int32), ("eval_threads", C.c_int32),
                 ("device", C.c_int32), ("profile", C.c_int32)]
+
+
+class ivs_server_cfg(C.Structure):
+    _fields_ = [("workspace_bytes", C.c_size_t), ("wave_children", C.c_int64), ("results_per_slot", C.c_int64),
+                ("max_slots", C.c_int32), ("max_vars", C.c_int32), ("sweeps_per_step", C.c_int32),
+                ("device", C.c_int32), ("reserve_factor", C.c_double)]
+
+
+class ivs_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("in_flight", C.c_int64), ("waiting", C.c_int64), ("steps", C.c_int64), ("sweeps", C.c_int64),
+                ("boxes", C.c_int64), ("busy_s", C.c_double), ("last_error", C.c_char * 160)]
 
 
 class ivs_kernel_time(C.Structure):
@@ -75,10 +87,20 @@ SIGNATURES = {
     "ivs_plan_stats": (C.c_int, [_VP, C.POINTER(ivs_stats)]),
     "ivs_plan_destroy": (None, [_VP]),
     "ivs_plan_kernel_times": (C.c_int32, [_VP, _VP, C.c_int32]),
+    "ivs_autotune": (C.c_int, [C.c_int32, C.POINTER(ivs_system), _VP, _VP, C.POINTER(ivs_options), C.c_int32,
+                               C.c_int64, C.POINTER(ivs_plan_cfg), C.POINTER(C.c_double)]),
     "ivs_probe_rate": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "ivs_solve_noalloc": (C.c_int, [C.POINTER(ivs_system), _VP, _VP, C.POINTER(ivs_options), _VP, _VP, _VP,
                                     _VP, C.c_int64, C.POINTER(C.c_int64), C.POINTER(ivs_stats), C.c_char_p,
                                     C.c_int32]),
+    "ivs_server_cfg_default": (None, [C.POINTER(ivs_server_cfg)]),
+    "ivs_server_create": (C.c_int, [C.POINTER(ivs_server_cfg), _PP]),
+    "ivs_server_submit": (C.c_int, [_VP, C.POINTER(ivs_system), _VP, _VP, C.POINTER(ivs_options),
+                                    C.POINTER(C.c_uint64)]),
+    "ivs_server_poll": (C.c_int, [_VP, C.c_uint64, _PP]),
+    "ivs_server_wait": (C.c_int, [_VP, C.c_uint64, C.c_double, _PP]),
+    "ivs_server_get_stats": (C.c_int, [_VP, C.POINTER(ivs_server_stats)]),
+    "ivs_server_destroy": (None, [_VP]),
     "ivs_status_str": (C.c_char_p, [C.c_int]),
     "ivs_last_error": (C.c_char_p, []),
 }
@@ -268,6 +290,88 @@ def probe_rate(kind=0, device=0):
     ms = C.c_double()
     _check(load().ivs_probe_rate(int(kind), int(device), C.byref(ops), C.byref(ms)))
     return ops.value, ms.value
+
+
+class Server:
+    """Continuous-batching server (``ivs_server_*``): submit systems while others run;
+    poll or wait for their results."""
+
+    def __init__(self, workspace_bytes=0, wave_children=0, results_per_slot=0, max_slots=0, max_vars=0,
+                 sweeps_per_step=0, device=0, reserve_factor=0.0):
+        lib = load()
+        self._lib = lib
+        cfg = ivs_server_cfg()
+        lib.ivs_server_cfg_default(C.byref(cfg))
+        for k, v in (("workspace_bytes", workspace_bytes), ("wave_children", wave_children),
+                     ("results_per_slot", results_per_slot), ("max_slots", max_slots), ("max_vars", max_vars),
+                     ("sweeps_per_step", sweeps_per_step), ("reserve_factor", reserve_factor)):
+            if v:
+                setattr(cfg, k, v)
+        cfg.device = int(device)
+        self.p = C.c_void_p()
+        self._refs = {}
+        _check(lib.ivs_server_create(C.byref(cfg), C.byref(self.p)))
+
+    def submit(self, s, **opts):
+        ref = _SysRef(s)
+        o = make_options(**{"tol": s.tol, **opts})
+        t = C.c_uint64()
+        _check(self._lib.ivs_server_submit(self.p, C.byref(ref.c), _ptr(ref.lo), _ptr(ref.hi), C.byref(o), C.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        r = C.c_void_p()
+        _check(self._lib.ivs_server_poll(self.p, C.c_uint64(ticket), C.byref(r)))
+        if not r:
+            return None
+        try:
+            return result_to_dict(r)
+        finally:
+            self._lib.ivs_result_free(r)
+
+    def wait(self, ticket, timeout_s=0.0):
+        r = C.c_void_p()
+        _check(self._lib.ivs_server_wait(self.p, C.c_uint64(ticket), float(timeout_s), C.byref(r)))
+        if not r:
+            return None
+        try:
+            return result_to_dict(r)
+        finally:
+            self._lib.ivs_result_free(r)
+
+    def stats(self):
+        st = ivs_server_stats()
+        _check(self._lib.ivs_server_get_stats(self.p, C.byref(st)))
+        d = {k: getattr(st, k) for k, _ in ivs_server_stats._fields_}
+        d["last_error"] = st.last_error.decode(errors="replace")
+        return d
+
+    def close(self):
+        if self.p:
+            self._lib.ivs_server_destroy(self.p)
+            self.p = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(systems, trial_boxes=200_000, **opts):
+    """Best (wave_children, eval_blocks) for these systems by short trial solves."""
+    lib = load()
+    refs = [_SysRef(s) for s in systems]
+    n = len(systems)
+    arr = (ivs_system * n)(*[r.c for r in refs])
+    los = (C.c_void_p * n)(*[_ptr(r.lo) for r in refs])
+    his = (C.c_void_p * n)(*[_ptr(r.hi) for r in refs])
+    oarr = (ivs_options * n)(*[make_options(**{"tol": s.tol, **opts}) for s in systems])
+    cfg = ivs_plan_cfg()
+    rate = C.c_double()
+    _check(lib.ivs_autotune(n, arr, los, his, oarr, C.sizeof(ivs_options), int(trial_boxes), C.byref(cfg),
+                            C.byref(rate)))
+    return {"wave_children": cfg.wave_children, "eval_blocks": cfg.eval_blocks, "trial_boxes_per_s": rate.value}
 
 
 def solve_batch(systems, **opts):

@@ -16,210 +16,29 @@
 
 #include "../../include/ivsolve.h"
 #include "ivs_internal.h"
+#include "ivs_hostcore.h"
 #include "ivs_kernels.cuh"
 #include "ivs_tab.cuh"
 
 using namespace ivs;
+using namespace ivs::host;
 
 namespace {
-
-thread_local std::string g_last_error;
-
-int fail(int status, const std::string &msg) {
-    g_last_error = msg;
-    return status;
-}
-
-#define CUDA_TRY(expr)                                                                   \
-    do {                                                                                 \
-        cudaError_t e_ = (expr);                                                         \
-        if (e_ != cudaSuccess)                                                           \
-            return fail(IVS_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
-    } while (0)
-
-// ---- outward rounding on the host (exact, from an error-free product) --------------
-// p = RN(c * a); e = fma(c, a, -p) is the exact error (Dekker/Ogita-Rump-Oishi
-// TwoProduct), so the rounded-down product is p when e >= 0 and the next double below p
-// otherwise; symmetric for rounding up.
-double mul_down(double c, double a) {
-    double p = c * a;
-    double e = std::fma(c, a, -p);
-    return e < 0 ? std::nextafter(p, -INFINITY) : p;
-}
-double mul_up(double c, double a) {
-    double p = c * a;
-    double e = std::fma(c, a, -p);
-    return e > 0 ? std::nextafter(p, INFINITY) : p;
-}
-float to_float_down(double d) {
-    float f = (float)d;
-    if ((double)f > d) f = std::nextafter(f, -INFINITY);
-    return f;
-}
-float to_float_up(double d) {
-    float f = (float)d;
-    if ((double)f < d) f = std::nextafter(f, INFINITY);
-    return f;
-}
-
-// One system's polynomials before packing into a blob (local indices).
-struct SysBuild {
-    std::vector<int32_t> poly_off{0};
-    std::vector<double> clo, chi;
-    std::vector<uint32_t> tinfo;
-    std::vector<uint8_t> fac;
-};
-
-struct HostTables {
-    std::vector<DevSys> sys;
-    std::vector<char> blobs;   // 16-byte aligned blobs (layout: ivs_tab.cuh)
-};
-
-void add_term(SysBuild &b, double clo, double chi, const uint8_t *e, int n) {
-    b.clo.push_back(clo);
-    b.chi.push_back(chi);
-    const uint32_t start = (uint32_t)b.fac.size();
-    uint32_t cnt = 0;
-    for (int j = 0; j < n; j++)
-        if (e[j]) {
-            b.fac.push_back((uint8_t)((j << 4) | e[j]));
-            cnt++;
-        }
-    b.tinfo.push_back((start << 5) | cnt);
-}
-
-// packs a built system into the blob arena and fills the blob fields of d
-void pack_blob(HostTables &h, const SysBuild &b, DevSys &d) {
-    const int T = (int)b.clo.size(), P = (int)b.poly_off.size() - 1, F = (int)b.fac.size();
-    const BlobLayout L = blob_layout(T, P, F);
-    const size_t off = h.blobs.size();
-    h.blobs.resize(off + L.bytes, 0);
-    char *base = h.blobs.data() + off;
-    for (int t = 0; t < T; t++) {
-        const float4 cs = make_float4(to_float_down(b.clo[t]), to_float_up(b.clo[t]), to_float_down(b.chi[t]),
-                                      to_float_up(b.chi[t]));
-        std::memcpy(base + L.cs + 16u * t, &cs, 16);
-        const float c32[2] = {to_float_down(b.clo[t]), to_float_up(b.chi[t])};
-        std::memcpy(base + L.clo32 + 4u * t, &c32[0], 4);
-        std::memcpy(base + L.chi32 + 4u * t, &c32[1], 4);
-    }
-    if (T) {
-        std::memcpy(base + L.clo, b.clo.data(), 8u * T);
-        std::memcpy(base + L.chi, b.chi.data(), 8u * T);
-        std::memcpy(base + L.tinfo, b.tinfo.data(), 4u * T);
-    }
-    std::memcpy(base + L.poly_off, b.poly_off.data(), 4u * (P + 1));
-    if (F) std::memcpy(base + L.fac, b.fac.data(), (size_t)F);
-    d.blob_off = (int64_t)off;
-    d.n_terms = T;
-    d.n_polys = P;
-    d.n_facs = F;
-    d.blob_bytes = (int32_t)L.bytes;
-}
-
-int validate(const ivs_system *s, const double *lo, const double *hi, const ivs_options *o) {
-    if (!s || !lo || !hi || !o) return fail(IVS_ERR_INVALID, "null argument");
-    if (s->n_vars <= 0 || s->n_vars > kMaxVars) return fail(IVS_ERR_INVALID, "n_vars must be in 1..16");
-    if (s->n_eqs <= 0 || s->n_terms < 0) return fail(IVS_ERR_INVALID, "n_eqs must be >= 1, n_terms >= 0");
-    if (!s->eq_offsets || (s->n_terms > 0 && (!s->coef_lo || !s->exps)))
-        return fail(IVS_ERR_INVALID, "null system array");
-    if (s->eq_offsets[0] != 0 || s->eq_offsets[s->n_eqs] != s->n_terms)
-        return fail(IVS_ERR_INVALID, "eq_offsets must run from 0 to n_terms");
-    for (int i = 0; i < s->n_eqs; i++)
-        if (s->eq_offsets[i + 1] < s->eq_offsets[i]) return fail(IVS_ERR_INVALID, "eq_offsets not monotone");
-    for (int t = 0; t < s->n_terms; t++) {
-        double a = s->coef_lo[t], b = s->coef_hi ? s->coef_hi[t] : a;
-        if (!std::isfinite(a) || !std::isfinite(b) || a > b) return fail(IVS_ERR_INVALID, "bad coefficient");
-        for (int j = 0; j < s->n_vars; j++)
-            if (s->exps[(size_t)t * s->n_vars + j] > kMaxExp) return fail(IVS_ERR_INVALID, "exponent > 15");
-    }
-    for (int j = 0; j < s->n_vars; j++)
-        if (!std::isfinite(lo[j]) || !std::isfinite(hi[j]) || lo[j] > hi[j])
-            return fail(IVS_ERR_INVALID, "bad initial box");
-    if (o->hs_enable && s->n_eqs != s->n_vars) return fail(IVS_ERR_INVALID, "HS needs n_eqs == n_vars");
-    if (!(o->tol >= 0) || !std::isfinite(o->tol)) return fail(IVS_ERR_INVALID, "tol must be finite and >= 0");
-    if (o->hs_iters < 0 || o->max_depth < 0 || o->max_depth > 0xFFF0 || o->root_depth < 0 ||
-        o->root_depth > o->max_depth)
-        return fail(IVS_ERR_INVALID, "bad depth / iteration options");
+template <class T>
+int upload(void *&cursor, const std::vector<T> &v, const T *&dst, cudaStream_t st) {
+    dst = reinterpret_cast<const T *>(cursor);
+    if (!v.empty()) CUDA_TRY(cudaMemcpyAsync(cursor, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    cursor = (char *)cursor + align_up(std::max<size_t>(v.size() * sizeof(T), 1), 256);
     return IVS_OK;
 }
 
-// F_i and J_ij polynomials of one system appended to the tables.  J_ij = sum over terms t
-// of equation i with a_tj > 0 of [down(c_lo a_tj), up(c_hi a_tj)] x^(a_t - e_j), in term
-// order; its factors keep the variable order of the term.
-// The FP32 shadow may decide boxes only when no FP32 intermediate can overflow: every
-// term's magnitude over the initial box, times the number of terms, stays below 1e30
-// (float max ~3.4e38).  Otherwise the plain FP32 prefilter (sound under overflow) runs.
-bool shadow_safe(const ivs_system *s, const double *lo, const double *hi) {
-    const int n = s->n_vars;
-    for (int i = 0; i < s->n_eqs; i++) {
-        const int nt = s->eq_offsets[i + 1] - s->eq_offsets[i];
-        for (int t = s->eq_offsets[i]; t < s->eq_offsets[i + 1]; t++) {
-            double c = std::max(std::fabs(s->coef_lo[t]), std::fabs(s->coef_hi ? s->coef_hi[t] : s->coef_lo[t]));
-            double b = c;
-            for (int j = 0; j < n; j++) {
-                const int a = s->exps[(size_t)t * n + j];
-                const double m = std::max(std::fabs(lo[j]), std::fabs(hi[j]));
-                for (int q = 0; q < a; q++) b *= std::max(m, 1.0);
-            }
-            if (!(b * (nt + 1) < 1e30)) return false;
-        }
-    }
-    return true;
+const ivs_options *opt_at(const ivs_options *opts, int32_t stride, int s) {
+    return stride == 0 ? opts : (const ivs_options *)((const char *)opts + (size_t)stride * s);
 }
-
-void compile_system(HostTables &h, const ivs_system *s, const ivs_options *o) {
-    const int n = s->n_vars, m = s->n_eqs;
-    SysBuild bld;
-    DevSys d{};
-    d.n = n;
-    d.m = m;
-    d.f_poly = 0;
-    for (int i = 0; i < m; i++) {
-        for (int t = s->eq_offsets[i]; t < s->eq_offsets[i + 1]; t++) {
-            double clo = s->coef_lo[t], chi = s->coef_hi ? s->coef_hi[t] : clo;
-            add_term(bld, clo, chi, s->exps + (size_t)t * n, n);
-        }
-        bld.poly_off.push_back((int32_t)bld.clo.size());
-    }
-    d.j_poly = -1;
-    if (m == n) {
-        d.j_poly = m;
-        uint8_t e[kMaxVars];
-        for (int i = 0; i < m; i++)
-            for (int j = 0; j < n; j++) {
-                for (int t = s->eq_offsets[i]; t < s->eq_offsets[i + 1]; t++) {
-                    const uint8_t *a = s->exps + (size_t)t * n;
-                    if (a[j] == 0) continue;
-                    double clo = s->coef_lo[t], chi = s->coef_hi ? s->coef_hi[t] : clo;
-                    std::memcpy(e, a, (size_t)n);
-                    e[j] -= 1;
-                    add_term(bld, mul_down(clo, (double)a[j]), mul_up(chi, (double)a[j]), e, n);
-                }
-                bld.poly_off.push_back((int32_t)bld.clo.size());
-            }
-    }
-    d.tol = o->tol + 0.0;   // -0 -> +0
-    d.hs_enable = o->hs_enable ? 1 : 0;
-    d.hs_min_depth = o->hs_min_depth;
-    d.hs_iters = o->hs_iters > 0 ? o->hs_iters : 1;
-    d.max_depth = o->max_depth;
-    d.prefilter = o->prefilter_fp32 ? 1 : 0;
-    d.shadow = 0;
-    d.max_boxes = o->max_boxes;
-    pack_blob(h, bld, d);
-    h.sys.push_back(d);
-}
-
 }  // namespace
 
-struct ivs_result {
-    int status = IVS_OK;
-    int n = 0;
-    std::vector<double> lo, hi;
-    std::vector<int32_t> flags, depth;
-    ivs_stats st{};
-};
+
+
 
 struct ivs_plan {
     int n_sys = 0, n_max = 0, device = 0, num_sms = 0;
@@ -227,6 +46,7 @@ struct ivs_plan {
     std::vector<int> dims;                 // distinct n over systems (HS kernels to launch)
     std::vector<ivs_options> opts;
     std::vector<int> sys_n;
+    std::vector<int64_t> sys_out_base, sys_out_cap;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     void *ws = nullptr;
@@ -255,68 +75,6 @@ struct ivs_plan {
     int64_t *h_wave_limit = nullptr;       // pinned
 };
 
-namespace {
-
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-struct Layout {
-    size_t queue, stage, surv, out, ctl, stats, roots, total;
-};
-
-Layout layout_for(int n_sys, int n_max, int64_t W, int64_t Q, int64_t O) {
-    Layout L{};
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
-    L.queue = take((size_t)Q * (3 * n_max * sizeof(double) + 2 * sizeof(int32_t)) + 4 * 256);
-    L.stage = take((size_t)W * (3 * n_max * sizeof(double) + 2 * sizeof(int32_t)) + 4 * 256);
-    L.surv = take((size_t)(n_max + 2) * W * sizeof(Surv));
-    L.out = take((size_t)O * (2 * n_max * sizeof(double) + 3 * sizeof(int32_t)) + 4 * 256);
-    L.ctl = take(sizeof(WaveCtl));
-    L.stats = take((size_t)n_sys * ST_COUNT * sizeof(unsigned long long));
-    L.roots = take((size_t)n_sys * (2 * n_max * sizeof(double) + sizeof(int32_t)) + 2 * 256);
-    L.total = off;
-    return L;
-}
-
-DevQueue carve_queue(char *base, int64_t cap, int n_max) {
-    DevQueue q{};
-    size_t off = 0;
-    auto take = [&](size_t bytes) { char *p = base + off; off = align_up(off + bytes, 256); return p; };
-    q.lo = (double *)take((size_t)cap * n_max * sizeof(double));
-    q.mid = (double *)take((size_t)cap * n_max * sizeof(double));
-    q.hi = (double *)take((size_t)cap * n_max * sizeof(double));
-    q.sys = (int32_t *)take((size_t)cap * sizeof(int32_t));
-    q.meta = (uint32_t *)take((size_t)cap * sizeof(uint32_t));
-    q.cap = cap;
-    return q;
-}
-
-DevOut carve_out(char *base, int64_t cap, int n_max) {
-    DevOut o{};
-    size_t off = 0;
-    auto take = [&](size_t bytes) { char *p = base + off; off = align_up(off + bytes, 256); return p; };
-    o.lo = (double *)take((size_t)cap * n_max * sizeof(double));
-    o.hi = (double *)take((size_t)cap * n_max * sizeof(double));
-    o.sys = (int32_t *)take((size_t)cap * sizeof(int32_t));
-    o.flags = (int32_t *)take((size_t)cap * sizeof(int32_t));
-    o.depth = (int32_t *)take((size_t)cap * sizeof(int32_t));
-    o.cap = cap;
-    return o;
-}
-
-template <class T>
-int upload(void *&cursor, const std::vector<T> &v, const T *&dst, cudaStream_t st) {
-    dst = reinterpret_cast<const T *>(cursor);
-    if (!v.empty()) CUDA_TRY(cudaMemcpyAsync(cursor, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
-    cursor = (char *)cursor + align_up(std::max<size_t>(v.size() * sizeof(T), 1), 256);
-    return IVS_OK;
-}
-
-const ivs_options *opt_at(const ivs_options *opts, int32_t stride, int s) {
-    return stride == 0 ? opts : (const ivs_options *)((const char *)opts + (size_t)stride * s);
-}
-
-}  // namespace
 
 extern "C" {
 
@@ -347,7 +105,7 @@ const char *ivs_status_str(int s) {
     }
 }
 
-const char *ivs_last_error(void) { return g_last_error.c_str(); }
+const char *ivs_last_error(void) { return ivs::host::last_error(); }
 
 size_t ivs_workspace_bytes(int32_t n_sys, const ivs_system *systems, int64_t W, int64_t Q, int64_t O) {
     int n_max = 1;
@@ -389,7 +147,7 @@ int ivs_plan_create(int32_t n_sys, const ivs_system *systems, const double *cons
     for (int s = 0; s < n_sys; s++) {
         const ivs_options *o = opt_at(opts, opts_stride, s);
         int rc = validate(&systems[s], box_lo[s], box_hi[s], o);
-        if (rc) return fail(rc, "system " + std::to_string(s) + ": " + g_last_error);
+        if (rc) return fail(rc, "system " + std::to_string(s) + ": " + std::string(last_error()));
         p->n_max = std::max(p->n_max, (int)systems[s].n_vars);
         out_cap += o->max_results > 0 ? o->max_results : 0;
         p->opts.push_back(*o);
@@ -397,6 +155,7 @@ int ivs_plan_create(int32_t n_sys, const ivs_system *systems, const double *cons
         if (std::find(p->dims.begin(), p->dims.end(), systems[s].n_vars) == p->dims.end())
             p->dims.push_back(systems[s].n_vars);
         compile_system(h, &systems[s], o);
+        (void)0;
         h.sys.back().shadow = (o->prefilter_fp32 && std::getenv("IVS_NO_SHADOW") == nullptr &&
                                shadow_safe(&systems[s], box_lo[s], box_hi[s])) ? 1 : 0;
         if (o->time_budget_s > 0)
@@ -411,7 +170,15 @@ int ivs_plan_create(int32_t n_sys, const ivs_system *systems, const double *cons
         }
         root_depth.push_back(opt_at(opts, opts_stride, s)->root_depth);
     }
-    if (out_cap <= 0) out_cap = std::max<int64_t>(1 << 20, (int64_t)n_sys * 4096);
+    // each system owns a result region: max_results boxes, or a default
+    out_cap = 0;
+    for (int s = 0; s < n_sys; s++) {
+        const ivs_options *o = opt_at(opts, opts_stride, s);
+        const int64_t cap = o->max_results > 0 ? o->max_results : (n_sys == 1 ? ((int64_t)1 << 20) : ((int64_t)1 << 14));
+        h.sys[s].out_base = out_cap;
+        h.sys[s].out_cap = cap;
+        out_cap += cap;
+    }
 
     p->device = c.device;
     CUDA_TRY(cudaSetDevice(p->device));
@@ -462,6 +229,10 @@ int ivs_plan_create(int32_t n_sys, const ivs_system *systems, const double *cons
     p->d_box_lo = (double *)(ws + L.roots);
     p->d_box_hi = p->d_box_lo + (size_t)n_sys * p->n_max;
     p->d_root_depth = (int32_t *)(p->d_box_hi + (size_t)n_sys * p->n_max);
+    for (int s = 0; s < n_sys; s++) {
+        p->sys_out_base.push_back(h.sys[s].out_base);
+        p->sys_out_cap.push_back(h.sys[s].out_cap);
+    }
     p->wave_children = W;
     p->queue_cap = Q;
     p->out_cap = out_cap;
@@ -479,7 +250,12 @@ int ivs_plan_create(int32_t n_sys, const ivs_system *systems, const double *cons
     // one system: every kernel caches its blob in shared memory (if it fits)
     a.single = (n_sys == 1 && h.sys[0].blob_bytes <= 48 * 1024) ? 1 : 0;
     a.blob_smem = a.single ? h.sys[0].blob_bytes : 0;
-    CUDA_TRY(configure_eval_kernels(a.blob_smem));
+    int max_tv = 0;
+    for (const DevSys &d : h.sys)
+        if (d.shadow) max_tv = std::max(max_tv, d.n_tv);
+    if (std::getenv("IVS_NO_COMBO")) max_tv = 0;   // per-child shadow evaluation instead of tables
+    choose_eval_layout(a, max_tv);
+    CUDA_TRY(configure_eval_kernels(a));
     CUDA_TRY(cudaMemcpyAsync(p->d_box_lo, roots_lo.data(), roots_lo.size() * 8, cudaMemcpyHostToDevice, p->stream));
     CUDA_TRY(cudaMemcpyAsync(p->d_box_hi, roots_hi.data(), roots_hi.size() * 8, cudaMemcpyHostToDevice, p->stream));
     CUDA_TRY(cudaMemcpyAsync(p->d_root_depth, root_depth.data(), root_depth.size() * 4, cudaMemcpyHostToDevice, p->stream));
@@ -618,19 +394,20 @@ int ivs_plan_result(ivs_plan *p, int32_t s, ivs_result **out) {
     if (!p || !out || s < 0 || s >= p->n_sys) return fail(IVS_ERR_INVALID, "bad arguments");
     *out = nullptr;
     CUDA_TRY(cudaSetDevice(p->device));
-    const int64_t total = std::min<int64_t>(p->h_ctl->out_count, p->out_cap);
-    const int n = p->sys_n[s], nm = p->n_max;
-    std::vector<int32_t> sys(total), flags(total), depth(total);
-    std::vector<double> lo((size_t)total * nm), hi((size_t)total * nm);
+    const unsigned long long *sv = p->h_stats.data() + (size_t)s * ST_COUNT;
+    const int64_t total = std::min<int64_t>((int64_t)sv[ST_OUT], p->sys_out_cap[s]);
+    const int64_t base = p->sys_out_base[s];
+    const int n = p->sys_n[s];
+    std::vector<int32_t> flags(total), depth(total);
+    std::vector<double> lo((size_t)total * n), hi((size_t)total * n);
     const DevOut &o = p->args.out;
     if (total > 0) {
-        CUDA_TRY(cudaMemcpyAsync(sys.data(), o.sys, total * 4, cudaMemcpyDeviceToHost, p->stream));
-        CUDA_TRY(cudaMemcpyAsync(flags.data(), o.flags, total * 4, cudaMemcpyDeviceToHost, p->stream));
-        CUDA_TRY(cudaMemcpyAsync(depth.data(), o.depth, total * 4, cudaMemcpyDeviceToHost, p->stream));
+        CUDA_TRY(cudaMemcpyAsync(flags.data(), o.flags + base, total * 4, cudaMemcpyDeviceToHost, p->stream));
+        CUDA_TRY(cudaMemcpyAsync(depth.data(), o.depth + base, total * 4, cudaMemcpyDeviceToHost, p->stream));
         for (int j = 0; j < n; j++) {
-            CUDA_TRY(cudaMemcpyAsync(lo.data() + (size_t)j * total, o.lo + (size_t)j * o.cap, total * 8,
+            CUDA_TRY(cudaMemcpyAsync(lo.data() + (size_t)j * total, o.lo + (size_t)j * o.cap + base, total * 8,
                                      cudaMemcpyDeviceToHost, p->stream));
-            CUDA_TRY(cudaMemcpyAsync(hi.data() + (size_t)j * total, o.hi + (size_t)j * o.cap, total * 8,
+            CUDA_TRY(cudaMemcpyAsync(hi.data() + (size_t)j * total, o.hi + (size_t)j * o.cap + base, total * 8,
                                      cudaMemcpyDeviceToHost, p->stream));
         }
         CUDA_TRY(cudaStreamSynchronize(p->stream));
@@ -638,41 +415,58 @@ int ivs_plan_result(ivs_plan *p, int32_t s, ivs_result **out) {
     std::unique_ptr<ivs_result> r(new (std::nothrow) ivs_result());
     if (!r) return fail(IVS_ERR_NOMEM, "host allocation");
     r->n = n;
-    std::vector<int64_t> idx;
-    for (int64_t k = 0; k < total; k++)
-        if (sys[k] == s) idx.push_back(k);
-    auto key = [&](int64_t k, int j, bool upper) {
-        double v = (upper ? hi : lo)[(size_t)j * total + k];
-        return v == 0 ? 0.0 : v;
-    };
-    std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
-        for (int j = 0; j < n; j++) {
-            double x = key(a, j, false), y = key(b, j, false);
-            if (x != y) return x < y;
-            x = key(a, j, true);
-            y = key(b, j, true);
-            if (x != y) return x < y;
-        }
-        return false;
-    });
-    r->lo.resize(idx.size() * n);
-    r->hi.resize(idx.size() * n);
-    r->flags.resize(idx.size());
-    r->depth.resize(idx.size());
-    for (size_t q = 0; q < idx.size(); q++) {
-        for (int j = 0; j < n; j++) {
-            r->lo[q * n + j] = key(idx[q], j, false);
-            r->hi[q * n + j] = key(idx[q], j, true);
-        }
-        r->flags[q] = flags[idx[q]];
-        r->depth[q] = depth[idx[q]];
-    }
+    fill_sorted(r.get(), n, total, lo, hi, flags, depth);
     fill_stats(p, s, &r->st);
     const unsigned long long fl = p->h_stats[(size_t)s * ST_COUNT + ST_FLAGS];
     int status = p->run_status;
     if (status == IVS_OK && fl) status = IVS_ERR_BUDGET;
     r->status = status;
     *out = r.release();
+    return IVS_OK;
+}
+
+int ivs_autotune(int32_t n_sys, const ivs_system *systems, const double *const *box_lo,
+                 const double *const *box_hi, const ivs_options *opts, int32_t opts_stride,
+                 int64_t trial_boxes, ivs_plan_cfg *best, double *best_rate) {
+    if (n_sys <= 0 || !systems || !box_lo || !box_hi || !opts || !best || trial_boxes <= 0)
+        return fail(IVS_ERR_INVALID, "bad arguments");
+    std::vector<ivs_options> topt((size_t)n_sys);
+    for (int s = 0; s < n_sys; s++) {
+        topt[(size_t)s] = *opt_at(opts, opts_stride, s);
+        topt[(size_t)s].max_boxes = trial_boxes;
+        topt[(size_t)s].time_budget_s = 0;
+    }
+    int sms = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0));
+    const int64_t waves[3] = {(int64_t)1 << 20, (int64_t)1 << 22, (int64_t)1 << 24};
+    const int per_sm[3] = {4, 8, 16};
+    double best_r = -1.0;
+    ivs_plan_cfg bc{};
+    for (int wi = 0; wi < 3; wi++)
+        for (int bi = 0; bi < 3; bi++) {
+            ivs_plan_cfg c{};
+            c.wave_children = waves[wi];
+            c.eval_blocks = sms * per_sm[bi];
+            ivs_plan *p = nullptr;
+            int rc = ivs_plan_create(n_sys, systems, box_lo, box_hi, topt.data(), (int32_t)sizeof(ivs_options), &c, &p);
+            if (rc == IVS_ERR_NOMEM) continue;   // this size does not fit: try the others
+            if (rc) return rc;
+            rc = ivs_plan_run(p);                // warm-up (graph upload, caches)
+            if (rc == IVS_OK || rc == IVS_ERR_NOMEM) rc = ivs_plan_run(p);
+            ivs_stats st{};
+            ivs_plan_stats(p, &st);
+            ivs_plan_destroy(p);
+            if (rc != IVS_OK && rc != IVS_ERR_NOMEM) return rc;
+            if (rc != IVS_OK || st.device_ms <= 0) continue;
+            const double r = (double)st.boxes / (st.device_ms * 1e-3);
+            if (r > best_r) {
+                best_r = r;
+                bc = c;
+            }
+        }
+    if (best_r < 0) return fail(IVS_ERR_NOMEM, "no trial configuration fit");
+    *best = bc;
+    if (best_rate) *best_rate = best_r;
     return IVS_OK;
 }
 

@@ -321,23 +321,32 @@ __global__ void __launch_bounds__(128) k_hs(SweepArgs a) {
                 }
             }
         }
-        // accepted boxes
-        const unsigned ma = __ballot_sync(kFull, fate == 1);
-        if (ma) {
-            unsigned long long pos = 0;
-            if (lane == 0) pos = atomicAdd((unsigned long long *)&ctl->out_count, (unsigned long long)__popc(ma));
-            pos = __shfl_sync(kFull, pos, 0);
+        // accepted boxes, into the system's result region
+        const int sys0 = __shfl_sync(kFull, sys, 0);
+        const bool uniform = __all_sync(kFull, !active || sys == sys0);
+        {
+            const unsigned ma = __ballot_sync(kFull, fate == 1);
+            long long k = -1;
+            if (ma && uniform) {
+                unsigned long long pos = 0;
+                if (lane == 0) pos = atomicAdd(stat_ptr(a, sys0, ST_OUT), (unsigned long long)__popc(ma));
+                pos = __shfl_sync(kFull, pos, 0);
+                k = (long long)(pos + __popc(ma & lanemask_lt()));
+            } else if (fate == 1) {
+                k = (long long)atomicAdd(stat_ptr(a, sys, ST_OUT), 1ull);
+            }
             if (fate == 1) {
-                const long long k = (long long)(pos + __popc(ma & lanemask_lt()));
-                if (k < a.out.cap) {
+                const DevSys &Ss = a.tb.sys[sys];
+                if (k < Ss.out_cap) {
+                    const long long e = Ss.out_base + k;
 #pragma unroll
                     for (int j = 0; j < N; j++) {
-                        a.out.lo[j * a.out.cap + k] = Xlo[j];
-                        a.out.hi[j * a.out.cap + k] = Xhi[j];
+                        a.out.lo[j * a.out.cap + e] = Xlo[j];
+                        a.out.hi[j * a.out.cap + e] = Xhi[j];
                     }
-                    a.out.sys[k] = sys;
-                    a.out.flags[k] = flag;
-                    a.out.depth[k] = depth;
+                    a.out.sys[e] = sys;
+                    a.out.flags[e] = flag;
+                    a.out.depth[e] = depth;
                 } else {
                     atomicOr(stat_ptr(a, sys, ST_FLAGS), (unsigned long long)kFlagResultOverflow);
                 }
@@ -366,22 +375,21 @@ __global__ void __launch_bounds__(128) k_hs(SweepArgs a) {
                 }
             }
         }
-        // statistics: one atomic per warp when the warp holds a single system
-        const int sys0 = __shfl_sync(kFull, sys, 0);
-        const bool uniform = __all_sync(kFull, !active || sys == sys0);
-        unsigned v[7] = {st_app, st_empty, st_con, st_sing, (fate == 1 && flag != 4) ? 1u : 0u, st_uns,
-                         fate == 2 ? 1u : 0u};
-        const int slot[7] = {ST_HS_APPLIED, ST_HS_EMPTY, ST_HS_CONTRACTED, ST_HS_SINGULAR, ST_ACCEPTED,
-                             ST_UNSPLITTABLE, ST_SPLIT};
+        // statistics (new parents also enter the live count): one atomic per warp when
+        // the warp holds a single system
+        unsigned v[8] = {st_app, st_empty, st_con, st_sing, (fate == 1 && flag != 4) ? 1u : 0u, st_uns,
+                         fate == 2 ? 1u : 0u, fate == 2 ? 1u : 0u};
+        const int slot[8] = {ST_HS_APPLIED, ST_HS_EMPTY, ST_HS_CONTRACTED, ST_HS_SINGULAR, ST_ACCEPTED,
+                             ST_UNSPLITTABLE, ST_SPLIT, ST_LIVE};
         if (uniform) {
 #pragma unroll
-            for (int q = 0; q < 7; q++) {
+            for (int q = 0; q < 8; q++) {
                 const unsigned tot = __reduce_add_sync(kFull, v[q]);
                 if (lane == 0 && tot) atomicAdd(stat_ptr(a, sys0, slot[q]), (unsigned long long)tot);
             }
         } else if (active) {
 #pragma unroll
-            for (int q = 0; q < 7; q++)
+            for (int q = 0; q < 8; q++)
                 if (v[q]) atomicAdd(stat_ptr(a, sys, slot[q]), (unsigned long long)v[q]);
         }
     }

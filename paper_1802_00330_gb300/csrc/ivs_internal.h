@@ -30,6 +30,8 @@ enum Stat : int {
     ST_FLAGS,          // bit 0: results overflowed, bit 1: depth cut, bit 2: box budget hit
     ST_EVAL64,         // boxes that ran the FP64 evaluation
     ST_KEEP_SHADOW,    // boxes the FP32 shadow proved kept (no FP64 evaluation)
+    ST_OUT,            // accepted boxes of the system (its result region holds min(this, out_cap))
+    ST_LIVE,           // queue entries of the system (0 after a sweep: the system is solved)
     ST_COUNT
 };
 constexpr int64_t kFlagResultOverflow = 1, kFlagDepthCut = 2, kFlagBudget = 4;
@@ -48,6 +50,10 @@ struct DevSys {
     int64_t max_boxes;
     int64_t blob_off;      // byte offset of the system's blob
     int32_t n_terms, n_polys, n_facs, blob_bytes;
+    int64_t out_base;      // the system's result region: entries [out_base, out_base + out_cap)
+    int64_t out_cap;
+    int32_t n_fterms;      // terms of the equations F_i
+    int32_t n_tv;          // term-combination entries (0: no per-parent table)
 };
 
 struct DevTables {
@@ -88,6 +94,7 @@ struct WaveCtl {
     int64_t cand_cursor;
     int64_t waves;
     int64_t wave_limit;     // the device loop stops when waves reaches it
+    int64_t children;       // children the current sweep evaluates
 };
 
 // survivor of the evaluation: parent index in the queue, child index

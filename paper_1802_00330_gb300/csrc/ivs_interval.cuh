@@ -46,61 +46,85 @@ __device__ __forceinline__ bool f_neg(float x) { return x < 0.0f; }
 __device__ __forceinline__ ivd iv_add(ivd x, ivd y) { return {__dadd_rd(x.lo, y.lo), __dadd_ru(x.hi, y.hi)}; }
 __device__ __forceinline__ ivd iv_sub(ivd x, ivd y) { return {__dsub_rd(x.lo, y.hi), __dsub_ru(x.hi, y.lo)}; }
 
+// Products select their endpoint operands from the operands' sign classes (integer
+// selects) and always issue two round-down and two round-up multiplies: with one box
+// per lane, branching on signs would diverge across the warp and every diverged path
+// would re-issue its FP64 instructions at full warp cost.  The second pair only differs
+// from the first when both operands straddle 0.  Classes: P = lo >= 0, else N = hi <= 0,
+// else S (lo < 0 < hi); P is tested first, as in the serial definition.
 __device__ __forceinline__ ivd iv_mul(ivd x, ivd y) {
-    // classify by sign: x >= 0, x <= 0, or straddling (lo < 0 < hi)
-    const bool xp = !d_neg(x.lo), xn = !d_pos(x.hi);
-    const bool yp = !d_neg(y.lo), yn = !d_pos(y.hi);
-    if (xp) {
-        if (yp) return {__dmul_rd(x.lo, y.lo), __dmul_ru(x.hi, y.hi)};
-        if (yn) return {__dmul_rd(x.hi, y.lo), __dmul_ru(x.lo, y.hi)};
-        return {__dmul_rd(x.hi, y.lo), __dmul_ru(x.hi, y.hi)};
-    }
-    if (xn) {
-        if (yp) return {__dmul_rd(x.lo, y.hi), __dmul_ru(x.hi, y.lo)};
-        if (yn) return {__dmul_rd(x.hi, y.hi), __dmul_ru(x.lo, y.lo)};
-        return {__dmul_rd(x.lo, y.hi), __dmul_ru(x.lo, y.lo)};
-    }
-    if (yp) return {__dmul_rd(x.lo, y.hi), __dmul_ru(x.hi, y.hi)};
-    if (yn) return {__dmul_rd(x.hi, y.lo), __dmul_ru(x.lo, y.lo)};
-    return {d_min(__dmul_rd(x.lo, y.hi), __dmul_rd(x.hi, y.lo)),
-            d_max(__dmul_ru(x.lo, y.lo), __dmul_ru(x.hi, y.hi))};
+    const bool xp = !d_neg(x.lo), xn = !xp && !d_pos(x.hi), xs = !xp && !xn;
+    const bool yp = !d_neg(y.lo), yn = !yp && !d_pos(y.hi), ys = !yp && !yn;
+    // lower end: xP: (yP ? lo : hi) * y.lo;  xN: (yN ? hi : lo) * y.hi;
+    //            xS: yN ? hi * lo : lo * hi (and hi * lo as well when y straddles)
+    const double la = xp ? (yp ? x.lo : x.hi) : (yn ? x.hi : x.lo);
+    const double lb = xp ? y.lo : (xn ? y.hi : (yn ? y.lo : y.hi));
+    const double la2 = (xs && ys) ? x.hi : la, lb2 = (xs && ys) ? y.lo : lb;
+    // upper end: xP: (yN ? lo : hi) * y.hi;  xN: (yP ? hi : lo) * y.lo;
+    //            xS: yP ? hi * hi : lo * lo (and hi * hi as well when y straddles)
+    const double ua = xp ? (yn ? x.lo : x.hi) : (xn ? (yp ? x.hi : x.lo) : (yp ? x.hi : x.lo));
+    const double ub = xp ? y.hi : (xn ? y.lo : (yp ? y.hi : y.lo));
+    const double ua2 = (xs && ys) ? x.hi : ua, ub2 = (xs && ys) ? y.hi : ub;
+    return {d_min(__dmul_rd(la, lb), __dmul_rd(la2, lb2)), d_max(__dmul_ru(ua, ub), __dmul_ru(ua2, ub2))};
 }
 
 // point b times interval y (b a double): two products
 __device__ __forceinline__ ivd iv_smul(double b, ivd y) {
-    if (!d_neg(b)) return {__dmul_rd(b, y.lo), __dmul_ru(b, y.hi)};
-    return {__dmul_rd(b, y.hi), __dmul_ru(b, y.lo)};
+    const bool neg = d_neg(b);
+    return {__dmul_rd(b, neg ? y.hi : y.lo), __dmul_ru(b, neg ? y.lo : y.hi)};
+}
+
+__device__ __forceinline__ double d_abs(double x) {
+    return __longlong_as_double(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL);
 }
 
 // monotone chains for the power rule (argument >= 0)
 __device__ __forceinline__ double chain_rd(double x, int k) { double p = x; for (int i = 1; i < k; i++) p = __dmul_rd(p, x); return p; }
 __device__ __forceinline__ double chain_ru(double x, int k) { double p = x; for (int i = 1; i < k; i++) p = __dmul_ru(p, x); return p; }
 
-// x^k, k >= 1 (power rule: even k folds the sign, odd k is monotone)
+// x^k, k >= 1, by the power rule.  Even k: [down-chain(a), up-chain(b)] with
+// (a, b) = (lo, hi) if lo >= 0, (-hi, -lo) if hi <= 0, (0, max(-lo, hi)) otherwise.
+// Odd k, each end e: q <- e, then (k-1) times q <- r(q * |e|); since r(-z) = -r'(z)
+// exactly, this equals chain(e) for e >= 0 and -chain'(-e) for e < 0 (chain' in the
+// opposite direction), i.e. the serial rule, with no branch on the sign.
 __device__ __forceinline__ ivd iv_pow(ivd x, int k) {
     if (k == 1) return x;
     if ((k & 1) == 0) {
-        if (!d_neg(x.lo)) return {chain_rd(x.lo, k), chain_ru(x.hi, k)};
-        if (!d_pos(x.hi)) return {chain_rd(-x.hi, k), chain_ru(-x.lo, k)};
-        return {0.0, chain_ru(d_max(-x.lo, x.hi), k)};
+        const bool p = !d_neg(x.lo), n = !p && !d_pos(x.hi);
+        const double a = p ? x.lo : (n ? -x.hi : 0.0);
+        const double b = p ? x.hi : (n ? -x.lo : d_max(-x.lo, x.hi));
+        return {chain_rd(a, k), chain_ru(b, k)};
     }
-    double lo = !d_neg(x.lo) ? chain_rd(x.lo, k) : -chain_ru(-x.lo, k);
-    double hi = !d_neg(x.hi) ? chain_ru(x.hi, k) : -chain_rd(-x.hi, k);
+    const double al = d_abs(x.lo), ah = d_abs(x.hi);
+    double lo = x.lo, hi = x.hi;
+    for (int i = 1; i < k; i++) {
+        lo = __dmul_rd(lo, al);
+        hi = __dmul_ru(hi, ah);
+    }
     return {lo, hi};
 }
 
-// ordinary division, 0 not in y: the two quotients the signs select
-__device__ __forceinline__ ivd iv_div(ivd x, ivd y) {
-    const bool xp = !d_neg(x.lo), xn = !d_pos(x.hi);
-    if (d_pos(y.lo)) {           // y > 0
-        if (xp) return {__ddiv_rd(x.lo, y.hi), __ddiv_ru(x.hi, y.lo)};
-        if (xn) return {__ddiv_rd(x.lo, y.lo), __ddiv_ru(x.hi, y.hi)};
-        return {__ddiv_rd(x.lo, y.lo), __ddiv_ru(x.hi, y.lo)};
+// ordinary division, 0 not in y: one round-down and one round-up quotient, operands
+// selected by the signs (y > 0: xP [lo/hi, hi/lo], xN [lo/lo, hi/hi], xS [lo/lo, hi/lo];
+// y < 0: xP [hi/hi, lo/lo], xN [hi/lo, lo/hi], xS [hi/hi, lo/hi])
+__device__ __forceinline__ void div_operands(ivd x, ivd y, double &ln, double &ld, double &un, double &ud) {
+    const bool xp = !d_neg(x.lo), xn = !xp && !d_pos(x.hi);
+    if (d_pos(y.lo)) {
+        ln = x.lo;
+        ld = xp ? y.hi : y.lo;
+        un = x.hi;
+        ud = xn ? y.hi : y.lo;
+    } else {
+        ln = x.hi;
+        ld = xn ? y.lo : y.hi;
+        un = x.lo;
+        ud = xp ? y.lo : y.hi;
     }
-    // y < 0
-    if (xp) return {__ddiv_rd(x.hi, y.hi), __ddiv_ru(x.lo, y.lo)};
-    if (xn) return {__ddiv_rd(x.hi, y.lo), __ddiv_ru(x.lo, y.hi)};
-    return {__ddiv_rd(x.hi, y.hi), __ddiv_ru(x.lo, y.hi)};
+}
+__device__ __forceinline__ ivd iv_div(ivd x, ivd y) {
+    double ln, ld, un, ud;
+    div_operands(x, y, ln, ld, un, ud);
+    return {__ddiv_rd(ln, ld), __ddiv_ru(un, ud)};
 }
 
 // Extended division (eq 10).  Writes up to two pieces (ends may be infinite) and
@@ -108,24 +132,38 @@ __device__ __forceinline__ ivd iv_div(ivd x, ivd y) {
 // 0 in x and 0 in y -> whole line; y = [0,0], 0 not in x -> empty; x < 0: y = [c,0] ->
 // [hi/c, +inf), c < 0 < d -> (-inf, hi/d] u [hi/c, +inf), y = [0,d] -> (-inf, hi/d];
 // x > 0: y = [c,0] -> (-inf, lo/c], c < 0 < d -> (-inf, lo/c] u [lo/d, +inf),
-// y = [0,d] -> [lo/d, +inf).  Finite ends round outward.
+// y = [0,d] -> [lo/d, +inf).  Finite ends round outward.  Every case needs at most one
+// round-down and one round-up quotient; both are issued once with selected operands.
 __device__ __forceinline__ int iv_extdiv(ivd x, ivd y, ivd *p) {
     const double inf = __longlong_as_double(0x7FF0000000000000LL);
-    if (d_pos(y.lo) || d_neg(y.hi)) { p[0] = iv_div(x, y); return 1; }
-    if (!d_pos(x.lo) && !d_neg(x.hi)) { p[0] = {-inf, inf}; return 1; }
+    const bool ordinary = d_pos(y.lo) || d_neg(y.hi);
+    const bool whole = !ordinary && !d_pos(x.lo) && !d_neg(x.hi);
     const bool ylo0 = d_iszero(y.lo), yhi0 = d_iszero(y.hi);
+    const bool xneg = d_neg(x.hi);                    // else x > 0 in the extended cases
+    double ln, ld, un, ud;
+    div_operands(x, y, ln, ld, un, ud);
+    if (!ordinary) {
+        // rd quotient: x < 0: hi / c;  x > 0: lo / d.   ru quotient: x < 0: hi / d;  x > 0: lo / c
+        ln = xneg ? x.hi : x.lo;
+        ld = xneg ? y.lo : y.hi;
+        un = xneg ? x.hi : x.lo;
+        ud = xneg ? y.hi : y.lo;
+    }
+    const double qd = __ddiv_rd(ln, ld), qu = __ddiv_ru(un, ud);
+    if (ordinary) { p[0] = {qd, qu}; return 1; }
+    if (whole) { p[0] = {-inf, inf}; return 1; }
     if (ylo0 && yhi0) return 0;
-    if (d_neg(x.hi)) {
-        if (yhi0) { p[0] = {__ddiv_rd(x.hi, y.lo), inf}; return 1; }
-        if (ylo0) { p[0] = {-inf, __ddiv_ru(x.hi, y.hi)}; return 1; }
-        p[0] = {-inf, __ddiv_ru(x.hi, y.hi)};
-        p[1] = {__ddiv_rd(x.hi, y.lo), inf};
+    if (xneg) {
+        if (yhi0) { p[0] = {qd, inf}; return 1; }
+        if (ylo0) { p[0] = {-inf, qu}; return 1; }
+        p[0] = {-inf, qu};
+        p[1] = {qd, inf};
         return 2;
     }
-    if (yhi0) { p[0] = {-inf, __ddiv_ru(x.lo, y.lo)}; return 1; }
-    if (ylo0) { p[0] = {__ddiv_rd(x.lo, y.hi), inf}; return 1; }
-    p[0] = {-inf, __ddiv_ru(x.lo, y.lo)};
-    p[1] = {__ddiv_rd(x.lo, y.hi), inf};
+    if (yhi0) { p[0] = {-inf, qu}; return 1; }
+    if (ylo0) { p[0] = {qd, inf}; return 1; }
+    p[0] = {-inf, qu};
+    p[1] = {qd, inf};
     return 2;
 }
 
@@ -175,15 +213,21 @@ __device__ __forceinline__ shv sh_add(shv a, shv b) {
     return {__fadd_rd(a.ld, b.ld), __fadd_ru(a.lu, b.lu), __fadd_rd(a.hd, b.hd), __fadd_ru(a.hu, b.hu)};
 }
 
-// enclosure [rd(min), ru(max)] of the exact product of two values with enclosures
-// [ad, au] and [bd, bu]
-__device__ __forceinline__ float2 enc_mul(float ad, float au, float bd, float bu) {
-    const ivf r = fv_mul(ivf{ad, au}, ivf{bd, bu});
-    return make_float2(r.lo, r.hi);
+// Enclosure [rd32(min), ru32(max)] of the exact product of two FP64 values whose signs
+// are known (sa / sb: true for >= 0, false for <= 0) and whose enclosures are
+// [ad, au], [bd, bu].  The enclosures are first clamped to the known sign; then the
+// minimum is ad*bd (+,+), au*bd (+,-), ad*bu (-,+), au*bu (-,-) and the maximum the
+// mirror choice: two multiplies, operands picked by selects (no divergence).
+__device__ __forceinline__ float2 enc_mul_signed(float ad, float au, bool sa, float bd, float bu, bool sb) {
+    ad = sa ? fmaxf(ad, 0.0f) : ad;
+    au = sa ? au : fminf(au, 0.0f);
+    bd = sb ? fmaxf(bd, 0.0f) : bd;
+    bu = sb ? bu : fminf(bu, 0.0f);
+    return make_float2(__fmul_rd(sb ? ad : au, sa ? bd : bu), __fmul_ru(sb ? au : ad, sa ? bu : bd));
 }
 
-// sign class of an FP64 interval from its shadow: 1 = [L,H] >= 0 (L >= 0),
-// 2 = [L,H] <= 0 (H <= 0), 3 = L < 0 < H, 0 = not provable
+// sign class of an FP64 interval from its shadow: 1 = P (L >= 0), 2 = N (H <= 0),
+// 3 = S (L < 0 < H), 0 = not provable
 __device__ __forceinline__ int sh_class(const shv &x) {
     if (x.ld >= 0.0f) return 1;
     if (x.hu <= 0.0f) return 2;
@@ -191,57 +235,60 @@ __device__ __forceinline__ int sh_class(const shv &x) {
     return 0;
 }
 
-// FP64 product: L = rd64(min of the 4 end products), H = ru64(max); the proven sign
-// classes name the products that are the min and the max.
+// FP64 product L = rd64(min of the four end products), H = ru64(max): the proven classes
+// name the products (the same table as iv_mul); each is enclosed by enc_mul_signed.
+// Ends' signs: lo is >= 0 in class P, <= 0 otherwise; hi is <= 0 in class N, >= 0 otherwise.
 __device__ __forceinline__ shv sh_mul(shv x, shv y, bool &poison) {
     const int cx = sh_class(x), cy = sh_class(y);
-    if (cx == 0 || cy == 0) { poison = true; return {0.f, 0.f, 0.f, 0.f}; }
-    float2 l, h;
-    if (cx == 1) {
-        if (cy == 1) { l = enc_mul(x.ld, x.lu, y.ld, y.lu); h = enc_mul(x.hd, x.hu, y.hd, y.hu); }
-        else if (cy == 2) { l = enc_mul(x.hd, x.hu, y.ld, y.lu); h = enc_mul(x.ld, x.lu, y.hd, y.hu); }
-        else { l = enc_mul(x.hd, x.hu, y.ld, y.lu); h = enc_mul(x.hd, x.hu, y.hd, y.hu); }
-    } else if (cx == 2) {
-        if (cy == 1) { l = enc_mul(x.ld, x.lu, y.hd, y.hu); h = enc_mul(x.hd, x.hu, y.ld, y.lu); }
-        else if (cy == 2) { l = enc_mul(x.hd, x.hu, y.hd, y.hu); h = enc_mul(x.ld, x.lu, y.ld, y.lu); }
-        else { l = enc_mul(x.ld, x.lu, y.hd, y.hu); h = enc_mul(x.ld, x.lu, y.ld, y.lu); }
-    } else {
-        if (cy == 1) { l = enc_mul(x.ld, x.lu, y.hd, y.hu); h = enc_mul(x.hd, x.hu, y.hd, y.hu); }
-        else if (cy == 2) { l = enc_mul(x.hd, x.hu, y.ld, y.lu); h = enc_mul(x.ld, x.lu, y.ld, y.lu); }
-        else {
-            const float2 l1 = enc_mul(x.ld, x.lu, y.hd, y.hu), l2 = enc_mul(x.hd, x.hu, y.ld, y.lu);
-            const float2 h1 = enc_mul(x.ld, x.lu, y.ld, y.lu), h2 = enc_mul(x.hd, x.hu, y.hd, y.hu);
-            l = make_float2(fminf(l1.x, l2.x), fminf(l1.y, l2.y));
-            h = make_float2(fmaxf(h1.x, h2.x), fmaxf(h1.y, h2.y));
-        }
-    }
-    return {l.x, l.y, h.x, h.y};
+    poison |= (cx == 0) | (cy == 0);
+    const bool xp = cx == 1, xn = cx == 2, xs = cx == 3;
+    const bool yp = cy == 1, yn = cy == 2, ys = cy == 3;
+    const bool sxl = xp, sxh = !xn, syl = yp, syh = !yn;
+    // lower: x end (yP ? lo : hi) when xP, (yN ? hi : lo) otherwise; y end lo when xP,
+    // hi when xN, (yN ? lo : hi) when xS; second candidate (x.hi, y.lo) when both straddle
+    const bool lxh = xp ? !yp : yn;
+    const bool lyh = xp ? false : (xn ? true : !yn);
+    const bool uxh = xp ? !yn : yp;
+    const bool uyh = xp ? true : (xn ? false : yp);
+    const bool ss = xs && ys;
+    const float2 l1 = enc_mul_signed(lxh ? x.hd : x.ld, lxh ? x.hu : x.lu, lxh ? sxh : sxl,
+                                     lyh ? y.hd : y.ld, lyh ? y.hu : y.lu, lyh ? syh : syl);
+    const float2 l2 = enc_mul_signed(ss ? x.hd : (lxh ? x.hd : x.ld), ss ? x.hu : (lxh ? x.hu : x.lu),
+                                     ss ? sxh : (lxh ? sxh : sxl), ss ? y.ld : (lyh ? y.hd : y.ld),
+                                     ss ? y.lu : (lyh ? y.hu : y.lu), ss ? syl : (lyh ? syh : syl));
+    const float2 h1 = enc_mul_signed(uxh ? x.hd : x.ld, uxh ? x.hu : x.lu, uxh ? sxh : sxl,
+                                     uyh ? y.hd : y.ld, uyh ? y.hu : y.lu, uyh ? syh : syl);
+    const float2 h2 = enc_mul_signed(ss ? x.hd : (uxh ? x.hd : x.ld), ss ? x.hu : (uxh ? x.hu : x.lu),
+                                     ss ? sxh : (uxh ? sxh : sxl), ss ? y.hd : (uyh ? y.hd : y.ld),
+                                     ss ? y.hu : (uyh ? y.hu : y.lu), ss ? syh : (uyh ? syh : syl));
+    return {fminf(l1.x, l2.x), fminf(l1.y, l2.y), fmaxf(h1.x, h2.x), fmaxf(h1.y, h2.y)};
 }
 
-// x^k (k >= 1) by the power rule of iv_pow: each FP64 chain p <- r64(p * v) is enclosed
-// by the down chain of the lower enclosure end and the up chain of the upper end.
+// x^k (k >= 1) by the power rule of iv_pow.  Even k: the class picks the chain operands
+// (clamped to their known sign) and down / up chains enclose the FP64 chains.  Odd k:
+// the FP64 end is the monotone q-chain of iv_pow, so the q-chain of the lower enclosure
+// end rounded down and of the upper end rounded up enclose it, whatever the signs.
 __device__ __forceinline__ shv sh_pow(shv x, int k, bool &poison) {
     if (k == 1) return x;
     if ((k & 1) == 0) {
-        if (x.ld >= 0.0f)
-            return {fchain_rd(x.ld, k), fchain_ru(x.lu, k), fchain_rd(x.hd, k), fchain_ru(x.hu, k)};
-        if (x.hu <= 0.0f)
-            return {fchain_rd(-x.hu, k), fchain_ru(-x.hd, k), fchain_rd(-x.lu, k), fchain_ru(-x.ld, k)};
-        if (x.lu < 0.0f && x.hd > 0.0f) {
-            const float md = fmaxf(-x.lu, x.hd), mu = fmaxf(-x.ld, x.hu);
-            return {0.0f, 0.0f, fchain_rd(md, k), fchain_ru(mu, k)};
-        }
-        poison = true;
-        return {0.f, 0.f, 0.f, 0.f};
+        const int c = sh_class(x);
+        poison |= c == 0;
+        const bool p = c == 1, n = c == 2;
+        const float ad = p ? x.ld : (n ? -x.hu : 0.0f);
+        const float au = p ? x.lu : (n ? -x.hd : 0.0f);
+        const float bd = p ? fmaxf(x.hd, 0.0f) : (n ? -fminf(x.lu, 0.0f) : fmaxf(-x.lu, x.hd));
+        const float bu = p ? x.hu : (n ? -x.ld : fmaxf(-x.ld, x.hu));
+        return {fchain_rd(ad, k), fchain_ru(au, k), fchain_rd(bd, k), fchain_ru(bu, k)};
     }
-    shv r;
-    if (x.ld >= 0.0f) { r.ld = fchain_rd(x.ld, k); r.lu = fchain_ru(x.lu, k); }
-    else if (x.lu < 0.0f) { r.ld = -fchain_ru(-x.ld, k); r.lu = -fchain_rd(-x.lu, k); }
-    else { poison = true; return {0.f, 0.f, 0.f, 0.f}; }
-    if (x.hd >= 0.0f) { r.hd = fchain_rd(x.hd, k); r.hu = fchain_ru(x.hu, k); }
-    else if (x.hu < 0.0f) { r.hd = -fchain_ru(-x.hd, k); r.hu = -fchain_rd(-x.hu, k); }
-    else { poison = true; return {0.f, 0.f, 0.f, 0.f}; }
-    return r;
+    float ld = x.ld, lu = x.lu, hd = x.hd, hu = x.hu;
+    const float ald = fabsf(x.ld), alu = fabsf(x.lu), ahd = fabsf(x.hd), ahu = fabsf(x.hu);
+    for (int i = 1; i < k; i++) {
+        ld = __fmul_rd(ld, ald);
+        lu = __fmul_ru(lu, alu);
+        hd = __fmul_rd(hd, ahd);
+        hu = __fmul_ru(hu, ahu);
+    }
+    return {ld, lu, hd, hu};
 }
 
 }  // namespace ivs

@@ -31,22 +31,65 @@ __device__ __forceinline__ unsigned long long *stat_ptr(const SweepArgs &a, int 
 // sweep control
 // ------------------------------------------------------------------------------------
 
-// Pops K parents from the top: the worst case (every child kept and split again) must
-// fit both the staging queue (wave_children entries) and the queue itself.
-__global__ void k_wave_begin(SweepArgs a) {
-    if (threadIdx.x != 0) return;
+// Pops K parents from the top of the queue, as many as fit: the K popped parents'
+// children (2^n each, 1 for an initial box) must fit the sweep's budget W, and in the
+// worst case (every child kept and split again) the queue must hold them:
+// top - K + children <= cap.  One block scans the fan-outs of the top entries.
+constexpr int kBeginThreads = 1024;
+constexpr int kBeginPer = 64;       // entries per thread: a window of 65536 parents
+__global__ void __launch_bounds__(kBeginThreads) k_wave_begin(SweepArgs a) {
+    __shared__ long long s_sum[kBeginThreads];
+    __shared__ long long s_first;
     WaveCtl *c = a.ctl;
-    int64_t top = c->top;
-    int64_t fan = (int64_t)1 << a.max_fan_shift;
-    int64_t k = a.wave_children / fan;
-    if (k > top) k = top;
-    if (fan > 1) {
-        int64_t room = (a.q.cap - top) / (fan - 1);
-        if (k > room) k = room;
+    const int64_t top = c->top;
+    const int64_t window = top < (int64_t)kBeginThreads * kBeginPer ? top : (int64_t)kBeginThreads * kBeginPer;
+    const int t = threadIdx.x;
+    // entry i (0-based from the top) is queue index top - 1 - i
+    auto fan_of = [&](int64_t i) -> long long {
+        const int64_t e = top - 1 - i;
+        return (a.q.meta[e] & kRootFlag) ? 1 : (1ll << a.tb.sys[a.q.sys[e]].n);
+    };
+    long long local = 0;
+    for (int q = 0; q < kBeginPer; q++) {
+        const int64_t i = (int64_t)t * kBeginPer + q;
+        if (i < window) local += fan_of(i);
     }
-    if (k <= 0 && top > 0) { c->error = 1; k = 0; }
+    // inclusive scan of the per-thread sums (Hillis-Steele over the block)
+    s_sum[t] = local;
+    if (t == 0) s_first = window;
+    __syncthreads();
+    for (int off = 1; off < kBeginThreads; off <<= 1) {
+        const long long v = t >= off ? s_sum[t - off] : 0;
+        __syncthreads();
+        s_sum[t] += v;
+        __syncthreads();
+    }
+    long long pre = s_sum[t] - local;   // children of the entries before this thread's
+    const long long room = a.q.cap - top;
+    for (int q = 0; q < kBeginPer; q++) {
+        const int64_t i = (int64_t)t * kBeginPer + q;
+        if (i >= window) break;
+        pre += fan_of(i);
+        if (pre > a.wave_children || pre - (i + 1) > room) {
+            atomicMin(&s_first, (long long)i);
+            break;
+        }
+    }
+    __syncthreads();
+    if (t != 0) return;
+    const int64_t k = s_first;
+    int64_t children = 0;
+    if (k > 0) {
+        // children of the first k entries: recompute from the scan
+        const int tk = (int)((k - 1) / kBeginPer), qk = (int)((k - 1) % kBeginPer);
+        long long pre2 = tk > 0 ? s_sum[tk - 1] : 0;
+        for (int q = 0; q <= qk; q++) pre2 += fan_of((int64_t)tk * kBeginPer + q);
+        children = pre2;
+    }
+    if (k <= 0 && top > 0) c->error = 1;
     c->base = top - k;
     c->k = k;
+    c->children = children;
     c->cursor = 0;
     c->staged = 0;
     for (int n = 0; n <= kMaxVars; n++) { c->surv_count[n] = 0; c->hs_cursor[n] = 0; }
@@ -82,6 +125,7 @@ __global__ void k_seed_roots(SweepArgs a, const double *box_lo, const double *bo
         }
         a.q.sys[s] = s;
         a.q.meta[s] = kRootFlag | ((uint32_t)root_depth[s] & kDepthMask);
+        a.stats[(size_t)s * ST_COUNT + ST_LIVE] = 1;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         WaveCtl *c = a.ctl;
@@ -98,6 +142,26 @@ __global__ void k_seed_roots(SweepArgs a, const double *box_lo, const double *bo
         c->wave_limit = 0x7FFFFFFFFFFFFFFFLL;
         for (int n = 0; n <= kMaxVars; n++) { c->surv_count[n] = 0; c->hs_cursor[n] = 0; }
     }
+}
+
+// Serving: appends `count` initial boxes (one per newly admitted system) on top of the
+// queue between sweeps; one block.
+__global__ void k_admit(SweepArgs a, const double *box_lo, const double *box_hi, const int32_t *slot,
+                        const int32_t *root_depth, int count, int n_max) {
+    const int64_t top = a.ctl->top;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        const int64_t e = top + i;
+        for (int j = 0; j < n_max; j++) {
+            a.q.lo[j * a.q.cap + e] = box_lo[(size_t)i * n_max + j];
+            a.q.mid[j * a.q.cap + e] = box_hi[(size_t)i * n_max + j];
+            a.q.hi[j * a.q.cap + e] = box_hi[(size_t)i * n_max + j];
+        }
+        a.q.sys[e] = slot[i];
+        a.q.meta[e] = kRootFlag | ((uint32_t)root_depth[i] & kDepthMask);
+        a.stats[(size_t)slot[i] * ST_COUNT + ST_LIVE] = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) a.ctl->top = top + count;
 }
 
 __global__ void k_loop_cond(SweepArgs a, cudaGraphConditionalHandle h) {
@@ -138,6 +202,15 @@ struct ChildCoordShadow {
         return shv{e[2 * up][j], e[2 * up + 1][j], e[2 * up + 2][j], e[2 * up + 3][j]};
     }
 };
+// coordinate of factor f of a table entry: the half is bit f of the combination q
+struct ComboCoordShadow {
+    const float (*e)[kMaxVars];
+    unsigned q;
+    __device__ __forceinline__ shv operator()(unsigned j, int f) const {
+        const unsigned up = (q >> f) & 1u;
+        return shv{e[2 * up][j], e[2 * up + 1][j], e[2 * up + 2][j], e[2 * up + 3][j]};
+    }
+};
 // box held in shared memory, structure of arrays with the given stride
 struct BoxCoord {
     const double *X;
@@ -165,6 +238,8 @@ __device__ __forceinline__ void push_surv(const SweepArgs &a, WaveCtl *ctl, int 
 // to k_eval64), the plain FP32 prefilter (its survivors go to k_eval64), or FP64 only.
 __global__ void __launch_bounds__(kEvalThreads) k_eval(SweepArgs a) {
     extern __shared__ __align__(16) char s_blob[];
+    float4 *s_tv = reinterpret_cast<float4 *>(s_blob + (a.single ? a.blob_smem : 0)) +
+                   (size_t)(threadIdx.x >> 5) * a.tv_stride;
     __shared__ double s_p[kEvalWarps][3][kMaxVars];
     __shared__ float s_f[kEvalWarps][4][kMaxVars];
     __shared__ float s_e[kEvalWarps][6][kMaxVars];
@@ -189,6 +264,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(SweepArgs a) {
         const SysTab T = make_tab(a.single ? s_blob : a.tb.blobs + S.blob_off, S);
         const bool root = (meta & kRootFlag) != 0;
         const int depth = (int)(meta & kDepthMask) + (root ? 0 : 1);
+        if (lane == 0) atomicAdd(stat_ptr(a, sys, ST_LIVE), ~0ull);   // the parent leaves the queue
         if (S.max_boxes > 0) {
             unsigned long long done = *(volatile unsigned long long *)stat_ptr(a, sys, ST_BOXES);
             if ((long long)done >= S.max_boxes) {
@@ -221,12 +297,27 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(SweepArgs a) {
         __syncwarp();
         const unsigned fan = root ? 1u : (1u << n);
         unsigned cnt_pre = 0, cnt_ev = 0, cnt_64 = 0, cnt_sh = 0;
+        // per-parent term-combination table: when the fan-out fills warps and it fits
+        const bool use_tv = S.prefilter && S.shadow && S.n_tv > 0 && S.n_tv <= a.tv_stride && fan >= 32;
+        if (use_tv) {
+            for (int e = (int)lane; e < S.n_tv; e += 32) {
+                const uint32_t mp = T.tv_map[e];
+                s_tv[e] = term_shadow(T, (int)(mp >> 8), ComboCoordShadow{s_e[w], mp & 255u});
+            }
+            __syncwarp();
+        }
         for (unsigned c0 = 0; c0 < fan; c0 += 32) {
             const unsigned c = c0 + lane;
             const bool active = c < fan;
             bool keep = false, cand = false;
             if (active) {
-                if (S.prefilter && S.shadow) {
+                if (use_tv) {
+                    const int r = decide_from_table(T, S, s_tv, c);
+                    keep = r == 1;
+                    cand = r == 2;
+                    cnt_pre += r == 0 ? 1u : 0u;
+                    cnt_sh += keep ? 1u : 0u;
+                } else if (S.prefilter && S.shadow) {
                     const int r = decide_shadow(T, S, ChildCoordShadow{s_e[w], c});
                     keep = r == 1;
                     cand = r == 2;
@@ -359,24 +450,26 @@ static cudaError_t launch_hs(const SweepArgs &a, int n, int num_sms, cudaStream_
     }
 }
 
-cudaError_t configure_eval_kernels(int blob_smem) {
-    if (blob_smem > 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, blob_smem);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_eval64, cudaFuncAttributeMaxDynamicSharedMemorySize, blob_smem);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+size_t eval_smem_bytes(const SweepArgs &a) {
+    return (size_t)(a.single ? a.blob_smem : 0) + (size_t)a.eval_warps * a.tv_stride * sizeof(float4);
+}
+
+cudaError_t configure_eval_kernels(const SweepArgs &a) {
+    cudaError_t e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eval_smem_bytes(a));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_eval64, cudaFuncAttributeMaxDynamicSharedMemorySize, a.single ? a.blob_smem : 0);
+    return e;
 }
 
 cudaError_t launch_sweep(const SweepArgs &a, const int *hs_dims, int n_hs_dims, int eval_blocks,
                          int eval_threads, int num_sms, cudaStream_t st, cudaEvent_t *ev) {
     // ev (optional): n_hs_dims + 5 events recorded between the stages
     const size_t blob = a.single ? (size_t)a.blob_smem : 0;
+    (void)eval_threads;
     if (ev) cudaEventRecord(ev[0], st);
-    k_wave_begin<<<1, 32, 0, st>>>(a);
+    k_wave_begin<<<1, kBeginThreads, 0, st>>>(a);
     if (ev) cudaEventRecord(ev[1], st);
-    k_eval<<<eval_blocks, eval_threads, blob, st>>>(a);
+    k_eval<<<eval_blocks, a.eval_warps * 32, eval_smem_bytes(a), st>>>(a);
     if (ev) cudaEventRecord(ev[2], st);
     k_eval64<<<num_sms * 4, kEval64Threads, blob, st>>>(a);
     if (ev) cudaEventRecord(ev[3], st);
@@ -425,6 +518,12 @@ cudaError_t build_sweep_graph(const SweepArgs &a, const int *hs_dims, int n_hs_d
     }
     *out = g;
     return cudaSuccess;
+}
+
+cudaError_t launch_admit(const SweepArgs &a, const double *d_lo, const double *d_hi, const int32_t *d_slot,
+                         const int32_t *d_depth, int count, int n_max, cudaStream_t st) {
+    k_admit<<<1, 256, 0, st>>>(a, d_lo, d_hi, d_slot, d_depth, count, n_max);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_seed_roots(const SweepArgs &a, const double *d_box_lo, const double *d_box_hi,

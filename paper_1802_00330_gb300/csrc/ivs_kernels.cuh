@@ -32,10 +32,22 @@ struct SweepArgs {
     int32_t n_sys;
     int32_t single;              // 1: one system; kernels cache its blob in shared memory
     int32_t blob_smem;           // bytes of that blob
+    int32_t tv_stride;           // term-combination entries per warp region (0: no tables)
+    int32_t eval_warps;          // warps per block of k_eval
 };
 
-// sets the dynamic shared memory limit of the evaluation kernels (blob cache)
-cudaError_t configure_eval_kernels(int blob_smem);
+// dynamic shared memory of k_eval (blob cache + the warps' combination tables) and the
+// kernels' limits; tv_stride / eval_warps come from choose_eval_layout
+size_t eval_smem_bytes(const SweepArgs &a);
+cudaError_t configure_eval_kernels(const SweepArgs &a);
+// picks eval_warps and tv_stride for the largest table `max_tv` of the plan's systems
+inline void choose_eval_layout(SweepArgs &a, int max_tv) {
+    const size_t budget = 200 * 1024 - (size_t)(a.single ? a.blob_smem : 0);
+    int warps = 8;
+    while (warps > 1 && (size_t)warps * (size_t)max_tv * 16 > budget) warps--;
+    a.eval_warps = warps;
+    a.tv_stride = ((size_t)max_tv * 16 <= budget) ? max_tv : 0;
+}
 // kernels per sweep: 4 + n_hs_dims; ev (nullable) receives n_hs_dims + 4 stage events
 cudaError_t launch_sweep(const SweepArgs &a, const int *hs_dims, int n_hs_dims, int eval_blocks,
                          int eval_threads, int num_sms, cudaStream_t st, cudaEvent_t *ev);
@@ -48,6 +60,9 @@ cudaError_t build_sweep_graph(const SweepArgs &a, const int *hs_dims, int n_hs_d
 cudaError_t run_probe(int kind, int num_sms, double *ops, float *ms);
 cudaError_t launch_seed_roots(const SweepArgs &a, const double *d_box_lo, const double *d_box_hi,
                               const int32_t *d_root_depth, int n_sys, int n_max, cudaStream_t st);
+// appends initial boxes of newly admitted systems (slot ids) on top of the queue
+cudaError_t launch_admit(const SweepArgs &a, const double *d_lo, const double *d_hi, const int32_t *d_slot,
+                         const int32_t *d_depth, int count, int n_max, cudaStream_t st);
 // Hansen-Sengupta + accept/split kernel for dimension n (ivs_hs_*.cu)
 cudaError_t launch_hs_dim1(const SweepArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_hs_dim2(const SweepArgs &a, int num_sms, cudaStream_t st);

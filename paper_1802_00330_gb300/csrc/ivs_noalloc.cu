@@ -123,6 +123,8 @@ bool pack_static(const ivs_system *s, DevSys &d) {
     d.n_terms = T;
     d.n_polys = P;
     d.n_facs = F;
+    d.n_fterms = 0;   // no per-parent combination table (the evaluation takes the direct path)
+    d.n_tv = 0;
     d.blob_bytes = (int32_t)L.bytes;
     return true;
 }
@@ -289,6 +291,8 @@ extern "C" int ivs_solve_noalloc(const ivs_system *s, const double *box_lo, cons
     a.q = carve_q(Q);
     if (off > kScratch) return err(IVS_ERR_INVALID, "ivs_solve_noalloc: fixed scratch overflow");
     d.blob_off = 0;   // the blob arena starts at d_blob
+    d.out_base = 0;
+    d.out_cap = O;
     a.tb.sys = d_sys;
     a.tb.blobs = d_blob;
     a.ctl = d_ctl;
@@ -314,7 +318,8 @@ extern "C" int ivs_solve_noalloc(const ivs_system *s, const double *box_lo, cons
     NA_TRY(cudaMemcpyAsync(d_depth, &rd, 4, cudaMemcpyHostToDevice, st));
     // the array keeps the previous call's contents: clear what must start at zero
     NA_TRY(cudaMemsetAsync(d_stats, 0, (size_t)ST_COUNT * 8, st));
-    NA_TRY(configure_eval_kernels(d.blob_bytes));
+    choose_eval_layout(a, 0);
+    NA_TRY(configure_eval_kernels(a));
     NA_TRY(launch_seed_roots(a, d_lo, d_hi, d_depth, 1, n, st));   // also resets the control block
 
     // ---- sweep loop (host-driven: a graph would have to be instantiated, which allocates) ----
@@ -336,7 +341,7 @@ extern "C" int ivs_solve_noalloc(const ivs_system *s, const double *box_lo, cons
     unsigned long long hs[ST_COUNT];
     NA_TRY(cudaMemcpyAsync(hs, d_stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
     NA_TRY(cudaStreamSynchronize(st));
-    const int64_t produced = g_ctl.out_count;
+    const int64_t produced = (int64_t)hs[ST_OUT];
     const int64_t held = std::min<int64_t>(produced, O);
     const int64_t give = std::min<int64_t>(held, out_cap);
     if (give > 0) {

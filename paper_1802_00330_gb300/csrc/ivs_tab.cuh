@@ -18,11 +18,12 @@
 
 namespace ivs {
 
-// byte layout of a system blob with T terms, P polynomials and F factors
+// byte layout of a system blob with T terms, P polynomials, F factors, TF terms in the
+// equations F_i and E term-combination entries
 struct BlobLayout {
-    uint32_t cs, clo, chi, clo32, chi32, poly_off, tinfo, fac, bytes;
+    uint32_t cs, clo, chi, clo32, chi32, poly_off, tinfo, tv_off, tv_map, fac, bytes;
 };
-__host__ __device__ inline BlobLayout blob_layout(int T, int P, int F) {
+__host__ __device__ inline BlobLayout blob_layout(int T, int P, int F, int TF = 0, int E = 0) {
     BlobLayout L;
     uint32_t o = 0;
     L.cs = o;        o += 16u * T;
@@ -32,6 +33,8 @@ __host__ __device__ inline BlobLayout blob_layout(int T, int P, int F) {
     L.chi32 = o;     o += 4u * T;
     L.poly_off = o;  o += 4u * (P + 1);
     L.tinfo = o;     o += 4u * T;
+    L.tv_off = o;    o += 4u * (TF + 1);
+    L.tv_map = o;    o += 4u * E;
     L.fac = o;       o += (uint32_t)F;
     L.bytes = (o + 15u) & ~15u;
     return L;
@@ -43,11 +46,13 @@ struct SysTab {
     const float *clo32, *chi32;
     const int32_t *poly_off; // [P + 1] term ranges
     const uint32_t *tinfo;   // factor start << 5 | factor count
+    const int32_t *tv_off;   // [TF + 1]: first combination entry of each F term
+    const uint32_t *tv_map;  // [E]: term << 8 | combination of its variables' halves
     const uint8_t *fac;
 };
 
 __device__ __forceinline__ SysTab make_tab(const char *blob, const DevSys &S) {
-    const BlobLayout L = blob_layout(S.n_terms, S.n_polys, S.n_facs);
+    const BlobLayout L = blob_layout(S.n_terms, S.n_polys, S.n_facs, S.n_fterms, S.n_tv);
     SysTab t;
     t.cs = reinterpret_cast<const float4 *>(blob + L.cs);
     t.clo = reinterpret_cast<const double *>(blob + L.clo);
@@ -56,6 +61,8 @@ __device__ __forceinline__ SysTab make_tab(const char *blob, const DevSys &S) {
     t.chi32 = reinterpret_cast<const float *>(blob + L.chi32);
     t.poly_off = reinterpret_cast<const int32_t *>(blob + L.poly_off);
     t.tinfo = reinterpret_cast<const uint32_t *>(blob + L.tinfo);
+    t.tv_off = reinterpret_cast<const int32_t *>(blob + L.tv_off);
+    t.tv_map = reinterpret_cast<const uint32_t *>(blob + L.tv_map);
     t.fac = reinterpret_cast<const uint8_t *>(blob + L.fac);
     return t;
 }
@@ -87,7 +94,9 @@ __device__ __forceinline__ ivd poly64(const SysTab &T, int p, const Coord &x) {
                 fc = T.fac[f0 + f];
                 prod = iv_mul(prod, iv_pow(x(fc >> 4), (int)(fc & 15u)));
             }
-            v = iv_mul(cf, prod);
+            // a point coefficient c: [c,c] * prod equals c * prod (two products, not four);
+            // every lane evaluates the same term, so the test does not diverge
+            v = (cf.lo == cf.hi) ? iv_smul(cf.lo, prod) : iv_mul(cf, prod);
         }
         acc = (t == t0) ? v : iv_add(acc, v);
     }
@@ -174,6 +183,54 @@ __device__ __forceinline__ int decide_shadow(const SysTab &T, const DevSys &S, c
         if (poison) { undecided = true; continue; }
         if (F.ld > 0.0f || F.hu < 0.0f) return 0;        // lo64 > 0 or hi64 < 0
         if (!(F.lu <= 0.0f && F.hd >= 0.0f)) undecided = true;
+    }
+    return undecided ? 2 : 1;
+}
+
+// ---- per-parent term-combination table (FP32 shadow) ------------------------------------
+// Entry (t, q) is the shadow of term t over the child whose halves in the term's
+// variables are the bits of q (bit f <-> the term's f-th factor): exactly what
+// poly_shadow computes for term t of any such child.  A poisoned entry is stored as NaN,
+// which then makes the equation's sum NaN: it neither excludes nor proves a keep.
+template <class Coord>
+__device__ __forceinline__ float4 term_shadow(const SysTab &T, int t, const Coord &x) {
+    const float4 ce = T.cs[t];
+    const uint32_t info = T.tinfo[t];
+    const int nf = (int)(info & 31u), f0 = (int)(info >> 5);
+    if (nf == 0) return ce;
+    bool poison = false;
+    unsigned fc = T.fac[f0];
+    shv prod = sh_pow(x(fc >> 4, 0), (int)(fc & 15u), poison);
+    for (int f = 1; f < nf; f++) {
+        fc = T.fac[f0 + f];
+        prod = sh_mul(prod, sh_pow(x(fc >> 4, f), (int)(fc & 15u), poison), poison);
+    }
+    const shv v = sh_mul(shv{ce.x, ce.y, ce.z, ce.w}, prod, poison);
+    if (poison) {
+        const float nan = __int_as_float(0x7FC00000);
+        return make_float4(nan, nan, nan, nan);
+    }
+    return make_float4(v.ld, v.lu, v.hd, v.hu);
+}
+
+// FP32 shadow decision of child c from its parent's table tv (same result as
+// decide_shadow on the child): 0 exclude, 1 keep, 2 undecided
+__device__ __forceinline__ int decide_from_table(const SysTab &T, const DevSys &S, const float4 *tv, unsigned c) {
+    bool undecided = false;
+    for (int i = 0; i < S.m; i++) {
+        const int t0 = T.poly_off[S.f_poly + i], t1 = T.poly_off[S.f_poly + i + 1];
+        shv acc = {0.f, 0.f, 0.f, 0.f};
+        for (int t = t0; t < t1; t++) {
+            const uint32_t info = T.tinfo[t];
+            const int nf = (int)(info & 31u), f0 = (int)(info >> 5);
+            unsigned q = 0;
+            for (int f = 0; f < nf; f++) q |= ((c >> (T.fac[f0 + f] >> 4)) & 1u) << f;
+            const float4 v = tv[T.tv_off[t] + (int)q];
+            const shv sv = {v.x, v.y, v.z, v.w};
+            acc = (t == t0) ? sv : sh_add(acc, sv);
+        }
+        if (acc.ld > 0.0f || acc.hu < 0.0f) return 0;
+        if (!(acc.lu <= 0.0f && acc.hd >= 0.0f)) undecided = true;   // also NaN (poison)
     }
     return undecided ? 2 : 1;
 }

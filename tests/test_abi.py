@@ -88,3 +88,16 @@ def test_no_gpu_fails_loudly(lib):
     s = synth.config_n2()
     assert _call_solve(lib, s, s.box_lo, s.box_hi) == 5
     assert b"cuda" in lib.ivs_last_error().lower() or len(lib.ivs_last_error()) > 0
+
+
+def test_server_without_gpu_fails_loudly(lib):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    from paper_1802_00330_gb300 import _binding as B
+    with pytest.raises(B.IvsError) as e:
+        B.Server(workspace_bytes=1 << 26, max_slots=4)
+    assert e.value.status == 5

@@ -1,0 +1,103 @@
+"""Serving form: continuous batching over one shared device queue.
+
+Each result must be the same alone (ivs_solve) and in the mix (served while other
+systems of different sizes share the same sweeps), bit for bit; requests submitted
+while others are running are admitted and finish.
+"""
+
+import time
+
+import numpy as np
+import pytest
+
+from paper_1802_00330_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_00330_gb300 import _binding, build
+    build.build()
+    _binding.load()
+    return _binding
+
+
+def wait_all(sv, tickets, budget_s=180.0):
+    """Results of all tickets, or a failure once the overall budget is spent."""
+    deadline = time.time() + budget_s
+    out = []
+    for t in tickets:
+        left = deadline - time.time()
+        assert left > 0, "server did not finish in time: " + str(sv.stats())
+        r = sv.wait(t, timeout_s=left)
+        assert r is not None, "server did not finish in time: " + str(sv.stats())
+        out.append(r)
+    return out
+
+
+def same(a, b):
+    return (a["status"] == b["status"] and np.array_equal(a["lo"], b["lo"]) and np.array_equal(a["hi"], b["hi"])
+            and np.array_equal(a["flags"], b["flags"]) and a["stats"]["boxes"] == b["stats"]["boxes"])
+
+
+def mix_systems():
+    small = synth.config_batched(count=40, seed=31337, n_range=(2, 6))
+    return small
+
+
+def test_alone_equals_in_the_mix(B):
+    systems = mix_systems()
+    targets = [0, 7, 19, 33]
+    alone = {i: B.solve(systems[i]) for i in targets}
+    sv = B.Server(workspace_bytes=1 << 30, max_slots=64, wave_children=1 << 20, max_vars=8)
+    try:
+        tickets = [sv.submit(s) for s in systems]
+        results = wait_all(sv, tickets)
+        for i in targets:
+            assert same(results[i], alone[i]), i
+        for i in (3, 11, 25):
+            assert same(results[i], B.solve(systems[i])), i
+        st = sv.stats()
+        assert st["last_error"] == "", st["last_error"]
+        assert st["admitted"] == len(systems) and st["completed"] == len(systems)
+    finally:
+        sv.close()
+
+
+def test_requests_join_while_others_run(B):
+    systems = mix_systems()
+    big = synth.config_n6()
+    sv = B.Server(workspace_bytes=1 << 30, max_slots=16, wave_children=1 << 20, sweeps_per_step=1, max_vars=8)
+    try:
+        t_big = sv.submit(big)
+        time.sleep(0.002)
+        later = [sv.submit(s) for s in systems[:10]]
+        res_later = wait_all(sv, later)
+        res_big = wait_all(sv, [t_big])[0]
+        assert same(res_big, B.solve(big))
+        for s, r in zip(systems[:10], res_later):
+            assert same(r, B.solve(s))
+        # the per-request clocks are filled
+        assert res_big["stats"]["solve_ms"] > 0
+    finally:
+        sv.close()
+
+
+def test_poll_and_unknown_ticket(B):
+    sv = B.Server(workspace_bytes=1 << 28, max_slots=4, wave_children=1 << 18, max_vars=4)
+    try:
+        t = sv.submit(synth.config_n2())
+        r = None
+        deadline = time.time() + 60
+        while r is None and time.time() < deadline:
+            r = sv.poll(t)
+            time.sleep(0.001)
+        assert r is not None and r["status"] == 0 and len(r["lo"]) == 2
+        with pytest.raises(B.IvsError):
+            sv.poll(t)          # already handed out
+    finally:
+        sv.close()
