@@ -33,7 +33,8 @@ using Clock = std::chrono::steady_clock;
 
 namespace {
 
-constexpr uint32_t kBlobSlot = 48 * 1024;   // term-table bytes per slot
+constexpr uint32_t kBlobSlot = 128 * 1024;   // term-table bytes per slot (n = 12, 14 terms of degree 4
+                                             // per equation need about 50 KB)
 
 struct Request {
     uint64_t ticket = 0;
@@ -160,15 +161,19 @@ int ivs_server::init() {
     a.n_sys = S;
     a.single = 0;
     a.blob_smem = 0;
-    d_rlo = (double *)(base + L.roots);
-    d_rhi = d_rlo + (size_t)S * n_max;
-    d_rslot = (int32_t *)(d_rhi + (size_t)S * n_max);
-    d_rdepth = d_rslot + S;
+    // system records, term tables and the admission staging (S initial boxes, slot ids
+    // and depths) in a second allocation
     const size_t sys_bytes = align_up((size_t)S * sizeof(DevSys), 256);
-    CUDA_TRY(cudaMalloc(&tables, sys_bytes + (size_t)S * kBlobSlot));
+    const size_t blob_bytes = (size_t)S * kBlobSlot;
+    const size_t adm_bytes = (size_t)S * (2 * (size_t)n_max * sizeof(double) + 2 * sizeof(int32_t));
+    CUDA_TRY(cudaMalloc(&tables, sys_bytes + blob_bytes + adm_bytes));
     CUDA_TRY(cudaMemsetAsync(tables, 0, sys_bytes, stream));
     d_sys = (DevSys *)tables;
     d_blobs = (char *)tables + sys_bytes;
+    d_rlo = (double *)(d_blobs + blob_bytes);
+    d_rhi = d_rlo + (size_t)S * n_max;
+    d_rslot = (int32_t *)(d_rhi + (size_t)S * n_max);
+    d_rdepth = d_rslot + S;
     a.tb.sys = d_sys;
     a.tb.blobs = d_blobs;
     CUDA_TRY(cudaMallocHost((void **)&h_ctl, sizeof(WaveCtl)));
@@ -394,6 +399,7 @@ void ivs_server::loop() {
                 if (r) { r->status = IVS_ERR_CUDA; r->n = w.n; }
                 done[w.ticket] = r;
                 state[w.ticket] = 2;
+                stats.completed++;
             }
             waiting.clear();
             cv_done.notify_all();

@@ -101,3 +101,21 @@ def test_poll_and_unknown_ticket(B):
             sv.poll(t)          # already handed out
     finally:
         sv.close()
+
+
+def test_many_slots_and_a_large_admission_burst(B):
+    """More than 128 slots and hundreds of requests admitted in few steps: every
+    result equals the single-system solve."""
+    systems = synth.config_batched(count=300, seed=4242, n_range=(2, 3))
+    sv = B.Server(workspace_bytes=1 << 30, max_slots=512, wave_children=1 << 18, max_vars=3)
+    try:
+        tickets = [sv.submit(s) for s in systems]
+        results = wait_all(sv, tickets)
+        st = sv.stats()
+        assert st["last_error"] == "", st["last_error"]
+        assert st["admitted"] == len(systems)
+        for i in range(0, len(systems), 37):
+            assert same(results[i], B.solve(systems[i])), i
+        assert all(r["status"] == 0 for r in results)
+    finally:
+        sv.close()
