@@ -71,7 +71,7 @@ void add_term(SysBuild &b, double clo, double chi, const uint8_t *e, int n) {
             b.fac.push_back((uint8_t)((j << 4) | e[j]));
             cnt++;
         }
-    b.tinfo.push_back((start << 5) | cnt);
+    b.tinfo.push_back((start << 5) | cnt | (clo == chi ? kTermPoint : 0u));
 }
 
 // packs a built system into the blob arena and fills the blob fields of d
@@ -85,7 +85,7 @@ void pack_blob(HostTables &h, const SysBuild &b, DevSys &d, int n_fterms) {
     std::vector<uint32_t> tv_map;
     bool tv_ok = true;
     for (int t = 0; t < n_fterms && tv_ok; t++) {
-        const int nf = (int)(b.tinfo[t] & 31u);
+        const int nf = term_nf(b.tinfo[t]);
         if (nf > 8 || tv_off.back() + (1 << nf) > kMaxTermCombos) { tv_ok = false; break; }
         for (int q = 0; q < (1 << nf); q++) tv_map.push_back(((uint32_t)t << 8) | (uint32_t)q);
         tv_off.push_back(tv_off.back() + (1 << nf));

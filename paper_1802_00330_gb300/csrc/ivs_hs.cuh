@@ -2,15 +2,25 @@
 // survived the evaluation (Section 2.3 eq 14, 17-22; Algorithm 3; Gauss-Jordan of
 // Section 2.4; Algorithm 4 products; Algorithm 1 termination (II); Algorithm 2 split).
 //
-// Mapping: one thread per box, 32 boxes per warp taken from an atomic cursor so a
-// sweep's boxes spread over every SM.  GB300's FP64 pipe retires 2 lane-operations per
-// cycle per SM and charges a whole warp instruction whatever the number of active
-// lanes, so every lane of every FP64 instruction carries a different box; two or three
-// resident warps per SM already keep the pipe busy.  Matrices live in per-thread shared
-// memory (structure of arrays, conflict-free); the system's term table is cached in
-// shared memory when the plan holds one system.  Comparisons, sign tests, NaN and
-// finiteness checks run on the integer pipes.  Templated on n; the instantiations are
-// spread over several translation units (ivs_hs_*.cu).
+// Mapping: one block takes BB boxes at a time (32; 16 for n >= 15) from an atomic
+// cursor, and its NW warps share the work of those boxes.  Lane b of every warp always
+// works on box b, so each FP64 warp instruction carries BB different boxes; the warps
+// split what is independent within a box: the n^2 + n polynomials of J(X) and f(x), the
+// row updates of each Gauss-Jordan step, the columns of M = B J(X), and the
+// Gauss-Seidel products.  What is serial within a box (pivot choice, the fold of each
+// Gauss-Seidel row, extended division and intersection, accept / split) stays with the
+// box's owner thread (warp 0, lane b).
+//
+// Why: GB300's FP64 pipe charges a whole warp instruction whatever the number of active
+// lanes, and a sweep has few boxes (often less than one warp per SM), so one thread per
+// box leaves the kernel waiting on the dependent chain of a single box.  Sharing a box's
+// independent work among warps shortens that chain without adding FP64 instructions.
+// Every value is computed by the same operations in the same order as the serial
+// definition, so the results are unchanged.  Matrices live in shared memory (structure
+// of arrays over the chunk's boxes: element (k, b) at k * BB + b, conflict-free).
+// Comparisons, sign tests, NaN and finiteness checks run on the integer pipes.
+// Templated on n; the instantiations are spread over several translation units
+// (ivs_hs_*.cu).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -45,386 +55,515 @@ __device__ __forceinline__ long long d_abskey(double x) {
 __device__ __forceinline__ bool d_le(double a, double b) {
     return d_key(a) <= d_key(b) || (d_iszero(a) && d_iszero(b));
 }
+// numerically equal (-0 == +0; NaN never equals)
+__device__ __forceinline__ bool d_same(double a, double b) {
+    return __double_as_longlong(a) == __double_as_longlong(b) || (d_iszero(a) && d_iszero(b));
+}
 
-// per-thread scratch (doubles, structure of arrays with the block's thread stride T)
+// Shared-memory layout of a block: arrays of rows, each row BB values (one per box).
 template <int N>
-struct Scratch {
-    static constexpr int J = 0;              // 2 N N : J(X), then M = B J
-    static constexpr int G = 2 * N * N;      // N N   : Gauss-Jordan matrix, then B
-    static constexpr int X = 3 * N * N;      // 2 N   : box for the interpreter
-    static constexpr int DOUBLES = X + 2 * N;
-    static constexpr int INTS = 2 * N;       // row ids, then column slots
-    static constexpr size_t BYTES = (size_t)DOUBLES * 8 + (size_t)INTS * 4;
+struct Cfg {
+    static constexpr int BB = (N >= 15) ? 16 : 32;   // boxes per chunk
+    static constexpr int NW = (N <= 3) ? 4 : 8;      // warps per block
+    static constexpr int NT = NW * 32;
+    static constexpr int MIN_BLOCKS = (N <= 10) ? 2 : 1;
+    // doubles
+    static constexpr int XLO = 0;                    // N rows: box lo
+    static constexpr int XHI = XLO + N * BB;         // N: box hi
+    static constexpr int XC = XHI + N * BB;          // N: midpoint x = mid X
+    static constexpr int YLO = XC + N * BB;          // N: Gauss-Seidel result lo
+    static constexpr int YHI = YLO + N * BB;         // N: hi
+    static constexpr int JM = YHI + N * BB;          // 2 N^2: J(X), then M = B J(X), then products
+    static constexpr int FR = JM + 2 * N * N * BB;   // 2 N: f(x), then r = B f(x)
+    static constexpr int GB = FR + 2 * N * BB;       // N^2: mid J(X), Gauss-Jordan, then B
+    static constexpr int PIV = GB + N * N * BB;      // 1: pivot of the current step
+    static constexpr int DOUBLES = PIV + BB;
+    // ints
+    static constexpr int I_ROWID = 0;                // N: original row of each storage column
+    static constexpr int I_SLOT = N * BB;            // N: storage column of each original row
+    static constexpr int I_SYS = 2 * N * BB;         // system of the box
+    static constexpr int I_ITS = I_SYS + BB;         // HS sweeps the box gets
+    static constexpr int I_RUN = I_ITS + BB;         // box takes part in the current sweep
+    static constexpr int I_BAD = I_RUN + BB;         // singular preconditioner: sweep skipped
+    static constexpr int I_EMPTY = I_BAD + BB;       // Gauss-Seidel left no point: box dropped
+    static constexpr int INTS = I_EMPTY + BB;
+    static constexpr size_t BYTES = ((size_t)DOUBLES * 8 + (size_t)INTS * 4 + 15) & ~(size_t)15;
 };
 
-struct BoxS {
-    const double *X;
-    int T;
-    __device__ __forceinline__ ivd operator()(unsigned j) const { return ivd{X[(2 * j) * T], X[(2 * j + 1) * T]}; }
+// coordinate accessors over the chunk arrays (box b's column)
+template <int BB>
+struct BoxCol {
+    const double *lo, *hi;
+    __device__ __forceinline__ ivd operator()(unsigned j) const { return ivd{lo[j * BB], hi[j * BB]}; }
 };
-}  // namespace hsd
+template <int BB>
+struct ThinCol {
+    const double *c;
+    __device__ __forceinline__ ivd operator()(unsigned j) const {
+        const double v = c[j * BB];
+        return ivd{v, v};
+    }
+};
 
-// One Gauss-Seidel sweep on B f(x) + B J(X)(z - x) = 0 (eq 14, 21, 22).
-// Returns 0 (Xo written), 1 (empty), 2 (skipped: singular preconditioner).
+// One Gauss-Seidel sweep on B f(x) + B J(X)(z - x) = 0 (eq 14, 21, 22) for every box of
+// the chunk with I_RUN set, by all threads of the block.  Leaves the result in Y and
+// sets I_EMPTY (no root) or I_BAD (singular preconditioner: the sweep is skipped).
 template <int N>
-__device__ int hs_sweep(const SysTab &Tb, const DevSys &S, const double *Xlo, const double *Xhi,
-                        double *Xolo, double *Xohi, double *sm, int *smi, int T) {
-    using namespace hsd;
-    using L = Scratch<N>;
-    double *J = sm + L::J * T;
-    double *G = sm + L::G * T;
-    double *X = sm + L::X * T;
-    int *rowid = smi;
-    int *slot_of = smi + N * T;
-#pragma unroll
-    for (int j = 0; j < N; j++) {
-        X[(2 * j) * T] = Xlo[j];
-        X[(2 * j + 1) * T] = Xhi[j];
+__device__ __forceinline__ void hs_sweep_block(const SweepArgs &a, const char *blob_smem, double *sd, int *si,
+                                               int t) {
+    using C = Cfg<N>;
+    constexpr int BB = C::BB, NT = C::NT;
+    double *J = sd + C::JM;   // interval (i, j): lo at (2 (i N + j)) BB, hi at (2 (i N + j) + 1) BB
+    double *G = sd + C::GB;   // point (i, j) at (i N + j) BB
+    const int *run = si + C::I_RUN;
+    int *bad = si + C::I_BAD;
+    int *empty = si + C::I_EMPTY;
+
+    // J(X) from the derivative polynomials compiled on the host (units q < N^2), and
+    // f(x) at the midpoint as a thin-box evaluation (units N^2 + i)
+    for (int e = t; e < (N * N + N) * BB; e += NT) {
+        const int q = e / BB, b = e % BB;
+        if (!run[b]) continue;
+        const DevSys &S = a.tb.sys[si[C::I_SYS + b]];
+        const SysTab Tb = make_tab(blob_smem ? blob_smem : a.tb.blobs + S.blob_off, S);
+        if (q < N * N) {
+            const ivd v = poly64(Tb, S.j_poly + q, BoxCol<BB>{sd + C::XLO + b, sd + C::XHI + b});
+            J[(2 * q) * BB + b] = v.lo;
+            J[(2 * q + 1) * BB + b] = v.hi;
+        } else {
+            const int i = q - N * N;
+            const ivd v = poly64(Tb, S.f_poly + i, ThinCol<BB>{sd + C::XC + b});
+            sd[C::FR + (2 * i) * BB + b] = v.lo;
+            sd[C::FR + (2 * i + 1) * BB + b] = v.hi;
+        }
     }
-    // J(X) from the derivative polynomials compiled on the host
-    for (int q = 0; q < N * N; q++) {
-        const ivd v = poly64(Tb, S.j_poly + q, BoxS{X, T});
-        J[(2 * q) * T] = v.lo;
-        J[(2 * q + 1) * T] = v.hi;
-    }
+    __syncthreads();
     // A = mid(J(X)), round to nearest
-    bool bad = false;
-    for (int q = 0; q < N * N; q++) {
-        const double m = midpoint_rn(J[(2 * q) * T], J[(2 * q + 1) * T]);
-        bad |= !d_finite(m);
-        G[q * T] = m;
+    for (int e = t; e < N * N * BB; e += NT) {
+        const int q = e / BB, b = e % BB;
+        if (!run[b]) continue;
+        const double m = midpoint_rn(J[(2 * q) * BB + b], J[(2 * q + 1) * BB + b]);
+        if (!d_finite(m)) atomicOr(&bad[b], 1);
+        G[q * BB + b] = m;
     }
-    if (bad) return 2;
+    __syncthreads();
     // Gauss-Jordan with partial pivoting (Section 2.4), in place: after step k storage
     // column k holds column rowid[k] of the right half [.|I]; entries of identity columns
     // not yet touched are 0 and their updates are exact no-ops, so they are skipped
-#pragma unroll
-    for (int k = 0; k < N; k++) rowid[k * T] = k;
     for (int k = 0; k < N; k++) {
-        int piv = k;
-        long long best = d_abskey(G[(k * N + k) * T]);
-        if (best < 0) return 2;            // NaN diagonal: the serial search keeps it, singular
-        for (int i = k + 1; i < N; i++) {
-            const long long v = d_abskey(G[(i * N + k) * T]);
-            if (v > best) { best = v; piv = i; }
-        }
-        if (best <= 0 || best >= 0x7FF0000000000000LL) return 2;   // zero, NaN or infinite
-        if (piv != k) {
+        if (t < BB) {
+            const int b = t;
+            if (run[b] && !bad[b]) {
+                int piv = k;
+                long long best = d_abskey(G[(k * N + k) * BB + b]);
+                bool sing = best < 0;          // NaN diagonal: the serial search keeps it
+                if (!sing) {
+                    for (int i = k + 1; i < N; i++) {
+                        const long long v = d_abskey(G[(i * N + k) * BB + b]);
+                        if (v > best) { best = v; piv = i; }
+                    }
+                    sing = best <= 0 || best >= 0x7FF0000000000000LL;   // zero, NaN or infinite
+                }
+                if (sing) {
+                    bad[b] = 1;
+                } else {
+                    if (piv != k) {
 #pragma unroll
-            for (int j = 0; j < N; j++) {
-                const double t = G[(k * N + j) * T];
-                G[(k * N + j) * T] = G[(piv * N + j) * T];
-                G[(piv * N + j) * T] = t;
+                        for (int j = 0; j < N; j++) {
+                            const double tmp = G[(k * N + j) * BB + b];
+                            G[(k * N + j) * BB + b] = G[(piv * N + j) * BB + b];
+                            G[(piv * N + j) * BB + b] = tmp;
+                        }
+                        const int r = si[C::I_ROWID + k * BB + b];
+                        si[C::I_ROWID + k * BB + b] = si[C::I_ROWID + piv * BB + b];
+                        si[C::I_ROWID + piv * BB + b] = r;
+                    }
+                    sd[C::PIV + b] = G[(k * N + k) * BB + b];
+                }
             }
-            const int t = rowid[k * T];
-            rowid[k * T] = rowid[piv * T];
-            rowid[piv * T] = t;
         }
-        const double pv = G[(k * N + k) * T];
-        const double rp = __ddiv_rn(1.0, pv);                           // eq 23 (identity column)
-#pragma unroll
-        for (int j = 0; j < N; j++)
-            if (j != k) G[(k * N + j) * T] = __ddiv_rn(G[(k * N + j) * T], pv);   // eq 23
-        G[(k * N + k) * T] = rp;
-        for (int i = 0; i < N; i++) {                                  // eq 24
-            if (i == k) continue;
-            const double f = G[(i * N + k) * T];
+        __syncthreads();
+        // pivot row divided by the pivot (eq 23; its own column becomes 1 / pivot)
+        for (int e = t; e < N * BB; e += NT) {
+            const int j = e / BB, b = e % BB;
+            if (!run[b] || bad[b]) continue;
+            const double pv = sd[C::PIV + b];
+            G[(k * N + j) * BB + b] = __ddiv_rn(j == k ? 1.0 : G[(k * N + j) * BB + b], pv);
+        }
+        __syncthreads();
+        // elimination of column k from the other rows (eq 24), one row per unit
+        for (int e = t; e < N * BB; e += NT) {
+            const int i = e / BB, b = e % BB;
+            if (i == k || !run[b] || bad[b]) continue;
+            const double f = G[(i * N + k) * BB + b];
+            const double rp = G[(k * N + k) * BB + b];
 #pragma unroll
             for (int j = 0; j < N; j++)
-                if (j != k) G[(i * N + j) * T] = __dsub_rn(G[(i * N + j) * T], __dmul_rn(f, G[(k * N + j) * T]));
-            G[(i * N + k) * T] = __dsub_rn(0.0, __dmul_rn(f, rp));
+                if (j != k)
+                    G[(i * N + j) * BB + b] = __dsub_rn(G[(i * N + j) * BB + b], __dmul_rn(f, G[(k * N + j) * BB + b]));
+            G[(i * N + k) * BB + b] = __dsub_rn(0.0, __dmul_rn(f, rp));
         }
+        __syncthreads();
     }
     // storage column k is column rowid[k] of B: restore the column order
+    if (t < BB) {
+        const int b = t;
+        if (run[b] && !bad[b]) {
 #pragma unroll
-    for (int k = 0; k < N; k++) slot_of[rowid[k * T] * T] = k;
-    for (int i = 0; i < N; i++) {
+            for (int k = 0; k < N; k++) si[C::I_SLOT + si[C::I_ROWID + k * BB + b] * BB + b] = k;
+        }
+    }
+    __syncthreads();
+    for (int e = t; e < N * BB; e += NT) {
+        const int i = e / BB, b = e % BB;
+        if (!run[b] || bad[b]) continue;
         double rowv[N];
 #pragma unroll
-        for (int u = 0; u < N; u++) rowv[u] = G[(i * N + slot_of[u * T]) * T];
+        for (int u = 0; u < N; u++) rowv[u] = G[(i * N + si[C::I_SLOT + u * BB + b]) * BB + b];
+        bool nf = false;
 #pragma unroll
         for (int u = 0; u < N; u++) {
-            bad |= !d_finite(rowv[u]);
-            G[(i * N + u) * T] = rowv[u];
+            nf |= !d_finite(rowv[u]);
+            G[(i * N + u) * BB + b] = rowv[u];
         }
+        if (nf) atomicOr(&bad[b], 1);
     }
-    if (bad) return 2;
-    // x = mid(X); f(x) as a thin-box evaluation
-    double xc[N];
-#pragma unroll
-    for (int j = 0; j < N; j++) {
-        xc[j] = midpoint_rn(Xlo[j], Xhi[j]);
-        X[(2 * j) * T] = xc[j];
-        X[(2 * j + 1) * T] = xc[j];
-    }
-    ivd fx[N];
-    for (int i = 0; i < N; i++) fx[i] = poly64(Tb, S.f_poly + i, BoxS{X, T});
-    // M = B J(X) in place of J, column by column; r = B f(x) (Algorithm 4, outward,
-    // u = 1..n in order; starting from the first product equals starting from [0,0])
-    for (int j = 0; j < N; j++) {
+    __syncthreads();
+    // M = B J(X) in place of J, one column per unit; r = B f(x) in place of f (unit N)
+    // (Algorithm 4, outward, u = 1..n in order; starting from the first product equals
+    // starting from [0,0])
+    for (int e = t; e < (N + 1) * BB; e += NT) {
+        const int j = e / BB, b = e % BB;
+        if (!run[b] || bad[b]) continue;
         ivd col[N];
+        if (j < N) {
 #pragma unroll
-        for (int u = 0; u < N; u++) col[u] = ivd{J[(2 * (u * N + j)) * T], J[(2 * (u * N + j) + 1) * T]};
+            for (int u = 0; u < N; u++) col[u] = ivd{J[(2 * (u * N + j)) * BB + b], J[(2 * (u * N + j) + 1) * BB + b]};
+        } else {
+#pragma unroll
+            for (int u = 0; u < N; u++) col[u] = ivd{sd[C::FR + (2 * u) * BB + b], sd[C::FR + (2 * u + 1) * BB + b]};
+        }
         for (int i = 0; i < N; i++) {
-            ivd acc = iv_smul(G[(i * N) * T], col[0]);
+            ivd acc = iv_smul(G[(i * N) * BB + b], col[0]);
 #pragma unroll
-            for (int u = 1; u < N; u++) acc = iv_add(acc, iv_smul(G[(i * N + u) * T], col[u]));
-            J[(2 * (i * N + j)) * T] = acc.lo;
-            J[(2 * (i * N + j) + 1) * T] = acc.hi;
+            for (int u = 1; u < N; u++) acc = iv_add(acc, iv_smul(G[(i * N + u) * BB + b], col[u]));
+            double *dst = (j < N) ? J + (2 * (i * N + j)) * BB + b : sd + C::FR + (2 * i) * BB + b;
+            dst[0] = acc.lo;
+            dst[BB] = acc.hi;
         }
     }
-    ivd r[N];
-#pragma unroll
-    for (int i = 0; i < N; i++) {
-        ivd acc = iv_smul(G[(i * N) * T], fx[0]);
-#pragma unroll
-        for (int u = 1; u < N; u++) acc = iv_add(acc, iv_smul(G[(i * N + u) * T], fx[u]));
-        r[i] = acc;
-    }
-    // Gauss-Seidel (eq 21-22)
-#pragma unroll
-    for (int j = 0; j < N; j++) { Xolo[j] = Xlo[j]; Xohi[j] = Xhi[j]; }
-#pragma unroll
-    for (int i = 0; i < N; i++) {
-        ivd s = r[i];
+    __syncthreads();
+    // Gauss-Seidel (eq 21-22).  Row i folds r_i and the products M_ij (Y_j - x_j), j != i,
+    // in order j = 1..n; products with j > i use the box's own coordinates and are formed
+    // up front, those with j < i as soon as Y_j is final.  A product is written over M_ij,
+    // which nothing reads afterwards.
+    for (int e = t; e < N * BB; e += NT) {
+        const int i = e / BB, b = e % BB;
+        sd[C::YLO + i * BB + b] = sd[C::XLO + i * BB + b];
+        sd[C::YHI + i * BB + b] = sd[C::XHI + i * BB + b];
+        if (!run[b] || bad[b]) continue;
 #pragma unroll
         for (int j = 0; j < N; j++) {
-            if (j == i) continue;
-            const ivd mij = {J[(2 * (i * N + j)) * T], J[(2 * (i * N + j) + 1) * T]};
-            const ivd d = iv_sub(ivd{Xolo[j], Xohi[j]}, ivd{xc[j], xc[j]});
-            s = iv_add(s, iv_mul(mij, d));
+            if (j <= i) continue;
+            const double xc = sd[C::XC + j * BB + b];
+            const ivd d = iv_sub(ivd{sd[C::XLO + j * BB + b], sd[C::XHI + j * BB + b]}, ivd{xc, xc});
+            const ivd p = iv_mul(ivd{J[(2 * (i * N + j)) * BB + b], J[(2 * (i * N + j) + 1) * BB + b]}, d);
+            J[(2 * (i * N + j)) * BB + b] = p.lo;
+            J[(2 * (i * N + j) + 1) * BB + b] = p.hi;
         }
-        const ivd D = {J[(2 * (i * N + i)) * T], J[(2 * (i * N + i) + 1) * T]};
-        if (d_isnan(s.lo) || d_isnan(s.hi) || d_isnan(D.lo) || d_isnan(D.hi)) continue;
-        ivd pc[2];
-        const int np = iv_extdiv(s, D, pc);
-        double lo = 0.0, hi = 0.0;
-        bool any = false;
-        for (int q = 0; q < np; q++) {
-            const ivd Y = iv_sub(ivd{xc[i], xc[i]}, pc[q]);
-            const double a0 = d_max(Xlo[i], Y.lo), b0 = d_min(Xhi[i], Y.hi);
-            if (d_le(a0, b0)) {
-                lo = any ? d_min(lo, a0) : a0;
-                hi = any ? d_max(hi, b0) : b0;
-                any = true;
+    }
+    __syncthreads();
+    for (int i = 0; i < N; i++) {
+        if (t < BB) {
+            const int b = t;
+            if (run[b] && !bad[b] && !empty[b]) {
+                ivd s = {sd[C::FR + (2 * i) * BB + b], sd[C::FR + (2 * i + 1) * BB + b]};
+#pragma unroll
+                for (int j = 0; j < N; j++) {
+                    if (j == i) continue;
+                    s = iv_add(s, ivd{J[(2 * (i * N + j)) * BB + b], J[(2 * (i * N + j) + 1) * BB + b]});
+                }
+                const ivd D = {J[(2 * (i * N + i)) * BB + b], J[(2 * (i * N + i) + 1) * BB + b]};
+                if (!(d_isnan(s.lo) || d_isnan(s.hi) || d_isnan(D.lo) || d_isnan(D.hi))) {
+                    ivd pc[2];
+                    const int np = iv_extdiv(s, D, pc);
+                    const double xc = sd[C::XC + i * BB + b];
+                    const double xlo = sd[C::XLO + i * BB + b], xhi = sd[C::XHI + i * BB + b];
+                    double lo = 0.0, hi = 0.0;
+                    bool any = false;
+                    for (int q = 0; q < np; q++) {
+                        const ivd Y = iv_sub(ivd{xc, xc}, pc[q]);
+                        const double a0 = d_max(xlo, Y.lo), b0 = d_min(xhi, Y.hi);
+                        if (d_le(a0, b0)) {
+                            lo = any ? d_min(lo, a0) : a0;
+                            hi = any ? d_max(hi, b0) : b0;
+                            any = true;
+                        }
+                    }
+                    if (!any) {
+                        empty[b] = 1;
+                    } else {
+                        sd[C::YLO + i * BB + b] = lo;
+                        sd[C::YHI + i * BB + b] = hi;
+                    }
+                }
             }
         }
-        if (!any) return 1;
-        Xolo[i] = lo;
-        Xohi[i] = hi;
+        __syncthreads();
+        if (i + 1 < N) {
+            for (int e = t; e < N * BB; e += NT) {
+                const int i2 = e / BB, b = e % BB;
+                if (i2 <= i || !run[b] || bad[b] || empty[b]) continue;
+                const double xc = sd[C::XC + i * BB + b];
+                const ivd d = iv_sub(ivd{sd[C::YLO + i * BB + b], sd[C::YHI + i * BB + b]}, ivd{xc, xc});
+                const ivd p = iv_mul(ivd{J[(2 * (i2 * N + i)) * BB + b], J[(2 * (i2 * N + i) + 1) * BB + b]}, d);
+                J[(2 * (i2 * N + i)) * BB + b] = p.lo;
+                J[(2 * (i2 * N + i) + 1) * BB + b] = p.hi;
+            }
+            __syncthreads();
+        }
     }
-    return 0;
 }
+}  // namespace hsd
 
 template <int N>
-__global__ void __launch_bounds__(128) k_hs(SweepArgs a) {
+__global__ void __launch_bounds__(hsd::Cfg<N>::NT, hsd::Cfg<N>::MIN_BLOCKS) k_hs(SweepArgs a, int cache_blob) {
     using namespace hsd;
-    using L = Scratch<N>;
+    using C = Cfg<N>;
+    constexpr int BB = C::BB;
     extern __shared__ __align__(16) char smem[];
-    const int T = blockDim.x, tid = threadIdx.x;
-    const size_t blob_bytes = a.single ? (size_t)a.blob_smem : 0;
-    double *sm = reinterpret_cast<double *>(smem + blob_bytes) + tid;
-    int *smi = reinterpret_cast<int *>(reinterpret_cast<double *>(smem + blob_bytes) + (size_t)L::DOUBLES * T) + tid;
+    __shared__ long long s_base;
+    const int t = threadIdx.x, lane = (int)lane_id();
+    const size_t blob_bytes = cache_blob ? (size_t)a.blob_smem : 0;
+    double *sd = reinterpret_cast<double *>(smem + blob_bytes);
+    int *si = reinterpret_cast<int *>(sd + C::DOUBLES);
 
     WaveCtl *ctl = a.ctl;
     const int64_t count = ctl->surv_count[N];
-    if (count == 0) return;
-    if (a.single) {
+    if ((int64_t)blockIdx.x * BB >= count) return;   // not needed for this many boxes
+    if (cache_blob) {
         const DevSys &S0 = a.tb.sys[0];
-        copy_blob(smem, a.tb.blobs + S0.blob_off, (uint32_t)S0.blob_bytes);
-        __syncthreads();
+        copy_blob(smem, a.tb.blobs + S0.blob_off, (uint32_t)S0.blob_bytes);   // visible after the next barrier
     }
+    const char *blob_smem = cache_blob ? smem : nullptr;
     const Surv *list = a.surv + (size_t)N * a.surv_cap;
-    const unsigned lane = lane_id();
+    const bool owner = t < BB;   // owner thread of box b = t
     for (;;) {
-        // each warp takes the next 32 boxes, so every SM gets a share of a small sweep
-        unsigned long long ws = 0;
-        if (lane == 0) ws = atomicAdd((unsigned long long *)&ctl->hs_cursor[N], 32ull);
-        ws = __shfl_sync(kFull, ws, 0);
-        if ((long long)ws >= count) break;
-        const int64_t idx = (int64_t)ws + lane;
-        const bool active = idx < count;
-        int fate = 0;   // 0 none / dropped, 1 accepted, 2 new parent
-        int flag = 0, sys = 0, depth = 0;
-        double Xlo[N], Xhi[N], xm[N];
-        unsigned st_app = 0, st_empty = 0, st_con = 0, st_sing = 0, st_uns = 0;
-        if (active) {
-            const Surv sv = list[idx];
-            const int64_t pi = sv.parent;
-            sys = a.q.sys[pi];
-            const uint32_t meta = a.q.meta[pi];
-            const bool root = (meta & kRootFlag) != 0;
-            depth = (int)(meta & kDepthMask) + (root ? 0 : 1);
-            const DevSys S = a.tb.sys[sys];
-            const SysTab Tb = make_tab(a.single ? smem : a.tb.blobs + S.blob_off, S);
+        if (t == 0) s_base = (long long)atomicAdd((unsigned long long *)&ctl->hs_cursor[N], (unsigned long long)BB);
+        __syncthreads();
+        const long long base = s_base;
+        if (base >= count) break;
+        // the owners fetch their boxes: child `child` of queue entry `parent`
+        bool active = false, stopped = false, dropped = false;
+        int sys = 0, depth = 0;
+        unsigned st_app = 0, st_con = 0, st_sing = 0;
+        if (owner) {
+            const int b = t;
+            const long long idx = base + b;
+            active = idx < count;
+            int its = 0;
+            if (active) {
+                const Surv sv = list[idx];
+                const int64_t pi = sv.parent;
+                sys = a.q.sys[pi];
+                const uint32_t meta = a.q.meta[pi];
+                const bool root = (meta & kRootFlag) != 0;
+                depth = (int)(meta & kDepthMask) + (root ? 0 : 1);
+                const DevSys &S = a.tb.sys[sys];
 #pragma unroll
-            for (int j = 0; j < N; j++) {
-                const bool up = (sv.child >> j) & 1u;
-                Xlo[j] = up ? a.q.mid[j * a.q.cap + pi] : a.q.lo[j * a.q.cap + pi];
-                Xhi[j] = up ? a.q.hi[j * a.q.cap + pi] : a.q.mid[j * a.q.cap + pi];
+                for (int j = 0; j < N; j++) {
+                    const bool up = (sv.child >> j) & 1u;
+                    const double lo = up ? a.q.mid[j * a.q.cap + pi] : a.q.lo[j * a.q.cap + pi];
+                    const double hi = up ? a.q.hi[j * a.q.cap + pi] : a.q.mid[j * a.q.cap + pi];
+                    sd[C::XLO + j * BB + b] = lo;
+                    sd[C::XHI + j * BB + b] = hi;
+                    sd[C::XC + j * BB + b] = midpoint_rn(lo, hi);
+                }
+                if (S.hs_enable && depth >= S.hs_min_depth) its = S.hs_iters > 0 ? S.hs_iters : 1;
             }
-            bool dropped = false;
-            if (S.hs_enable && depth >= S.hs_min_depth) {
-                const int iters = S.hs_iters > 0 ? S.hs_iters : 1;
-                for (int it = 0; it < iters; it++) {
-                    st_app++;
-                    double Ylo[N], Yhi[N];
-                    const int rc = hs_sweep<N>(Tb, S, Xlo, Xhi, Ylo, Yhi, sm, smi, T);
-                    if (rc == 1) { dropped = true; break; }
-                    if (rc == 2) { st_sing++; break; }
+            si[C::I_SYS + b] = sys;
+            si[C::I_ITS + b] = its;
+        }
+        __syncthreads();
+        int max_it = 0;
+        for (int b = 0; b < BB; b++) max_it = max(max_it, si[C::I_ITS + b]);
+        for (int it = 0; it < max_it; it++) {
+            if (owner) {
+                const int b = t;
+                const bool run = active && !stopped && it < si[C::I_ITS + b];
+                si[C::I_RUN + b] = run ? 1 : 0;
+                si[C::I_BAD + b] = 0;
+                si[C::I_EMPTY + b] = 0;
+                st_app += run ? 1u : 0u;
+#pragma unroll
+                for (int k = 0; k < N; k++) si[C::I_ROWID + k * BB + b] = k;
+            }
+            __syncthreads();
+            hs_sweep_block<N>(a, blob_smem, sd, si, t);
+            if (owner && si[C::I_RUN + t]) {
+                const int b = t;
+                if (si[C::I_EMPTY + b]) {
+                    dropped = true;
+                    stopped = true;
+                } else if (si[C::I_BAD + b]) {
+                    st_sing++;
+                    stopped = true;
+                } else {
                     bool changed = false;
 #pragma unroll
                     for (int j = 0; j < N; j++) {
-                        changed |= (__double_as_longlong(Ylo[j]) != __double_as_longlong(Xlo[j]) && !(d_iszero(Ylo[j]) && d_iszero(Xlo[j]))) ||
-                                   (__double_as_longlong(Yhi[j]) != __double_as_longlong(Xhi[j]) && !(d_iszero(Yhi[j]) && d_iszero(Xhi[j])));
-                        Xlo[j] = Ylo[j];
-                        Xhi[j] = Yhi[j];
+                        const double ylo = sd[C::YLO + j * BB + b], yhi = sd[C::YHI + j * BB + b];
+                        changed |= !d_same(ylo, sd[C::XLO + j * BB + b]) || !d_same(yhi, sd[C::XHI + j * BB + b]);
+                        sd[C::XLO + j * BB + b] = ylo;
+                        sd[C::XHI + j * BB + b] = yhi;
+                        sd[C::XC + j * BB + b] = midpoint_rn(ylo, yhi);
                     }
                     st_con += changed ? 1u : 0u;
                 }
             }
-            if (dropped) {
-                st_empty++;
-            } else {
-                // Algorithm 1 termination (II): width test; otherwise split at midpoints
-                double w = 0.0;
-                int jw = 0;
-#pragma unroll
-                for (int j = 0; j < N; j++) {
-                    const double wj = __dsub_rn(Xhi[j], Xlo[j]);
-                    if (d_key(wj) > d_key(w)) { w = wj; jw = j; }
-                }
-                if (d_key(w) <= d_key(S.tol)) {
-                    fate = 1;
-                    flag = 1;
+            __syncthreads();
+        }
+        // Algorithm 1 termination (II) and the split, by warp 0 (lane b owns box b)
+        if (t < 32) {
+            const int b = t;
+            int fate = 0;   // 0 none / dropped, 1 accepted, 2 new parent
+            int flag = 0;
+            unsigned st_uns = 0, st_empty = 0;
+            if (active) {
+                const DevSys &S = a.tb.sys[sys];
+                if (dropped) {
+                    st_empty = 1;
                 } else {
+                    double w = 0.0;
+                    int jw = 0;
 #pragma unroll
-                    for (int j = 0; j < N; j++) xm[j] = midpoint_rn(Xlo[j], Xhi[j]);
-                    double mw = xm[0], lw = Xlo[0], hw = Xhi[0];
-#pragma unroll
-                    for (int j = 1; j < N; j++)
-                        if (j == jw) { mw = xm[j]; lw = Xlo[j]; hw = Xhi[j]; }
-                    if (d_le(mw, lw) && d_le(lw, mw)) {
+                    for (int j = 0; j < N; j++) {
+                        const double wj = __dsub_rn(sd[C::XHI + j * BB + b], sd[C::XLO + j * BB + b]);
+                        if (d_key(wj) > d_key(w)) { w = wj; jw = j; }
+                    }
+                    if (d_key(w) <= d_key(S.tol)) {
                         fate = 1;
-                        flag = 2;
-                        st_uns++;
-                    } else if (d_le(mw, hw) && d_le(hw, mw)) {
-                        fate = 1;
-                        flag = 2;
-                        st_uns++;
-                    } else if (depth + 1 > S.max_depth) {
-                        fate = 1;
-                        flag = 4;
+                        flag = 1;
                     } else {
-                        fate = 2;
+                        const double lw = sd[C::XLO + jw * BB + b], hw = sd[C::XHI + jw * BB + b];
+                        const double mw = midpoint_rn(lw, hw);
+                        if (d_le(mw, lw) && d_le(lw, mw)) {
+                            fate = 1;
+                            flag = 2;
+                            st_uns++;
+                        } else if (d_le(mw, hw) && d_le(hw, mw)) {
+                            fate = 1;
+                            flag = 2;
+                            st_uns++;
+                        } else if (depth + 1 > S.max_depth) {
+                            fate = 1;
+                            flag = 4;
+                        } else {
+                            fate = 2;
+                        }
                     }
                 }
             }
-        }
-        // accepted boxes, into the system's result region
-        const int sys0 = __shfl_sync(kFull, sys, 0);
-        const bool uniform = __all_sync(kFull, !active || sys == sys0);
-        {
-            const unsigned ma = __ballot_sync(kFull, fate == 1);
-            long long k = -1;
-            if (ma && uniform) {
+            // accepted boxes, into the system's result region
+            const int sys0 = __shfl_sync(kFull, sys, 0);
+            const bool uniform = __all_sync(kFull, !active || sys == sys0);
+            {
+                const unsigned ma = __ballot_sync(kFull, fate == 1);
+                long long k = -1;
+                if (ma && uniform) {
+                    unsigned long long pos = 0;
+                    if (lane == 0) pos = atomicAdd(stat_ptr(a, sys0, ST_OUT), (unsigned long long)__popc(ma));
+                    pos = __shfl_sync(kFull, pos, 0);
+                    k = (long long)(pos + __popc(ma & lanemask_lt()));
+                } else if (fate == 1) {
+                    k = (long long)atomicAdd(stat_ptr(a, sys, ST_OUT), 1ull);
+                }
+                if (fate == 1) {
+                    const DevSys &Ss = a.tb.sys[sys];
+                    if (k < Ss.out_cap) {
+                        const long long e = Ss.out_base + k;
+#pragma unroll
+                        for (int j = 0; j < N; j++) {
+                            a.out.lo[j * a.out.cap + e] = sd[C::XLO + j * BB + b];
+                            a.out.hi[j * a.out.cap + e] = sd[C::XHI + j * BB + b];
+                        }
+                        a.out.sys[e] = sys;
+                        a.out.flags[e] = flag;
+                        a.out.depth[e] = depth;
+                    } else {
+                        atomicOr(stat_ptr(a, sys, ST_FLAGS), (unsigned long long)kFlagResultOverflow);
+                    }
+                    if (flag == 4) atomicOr(stat_ptr(a, sys, ST_FLAGS), (unsigned long long)kFlagDepthCut);
+                }
+            }
+            // new parents (the split midpoints are the box midpoints)
+            const unsigned ms = __ballot_sync(kFull, fate == 2);
+            if (ms) {
                 unsigned long long pos = 0;
-                if (lane == 0) pos = atomicAdd(stat_ptr(a, sys0, ST_OUT), (unsigned long long)__popc(ma));
+                if (lane == 0) pos = atomicAdd((unsigned long long *)&ctl->staged, (unsigned long long)__popc(ms));
                 pos = __shfl_sync(kFull, pos, 0);
-                k = (long long)(pos + __popc(ma & lanemask_lt()));
-            } else if (fate == 1) {
-                k = (long long)atomicAdd(stat_ptr(a, sys, ST_OUT), 1ull);
-            }
-            if (fate == 1) {
-                const DevSys &Ss = a.tb.sys[sys];
-                if (k < Ss.out_cap) {
-                    const long long e = Ss.out_base + k;
+                if (fate == 2) {
+                    const long long k = (long long)(pos + __popc(ms & lanemask_lt()));
+                    if (k < a.stage.cap) {
 #pragma unroll
-                    for (int j = 0; j < N; j++) {
-                        a.out.lo[j * a.out.cap + e] = Xlo[j];
-                        a.out.hi[j * a.out.cap + e] = Xhi[j];
+                        for (int j = 0; j < N; j++) {
+                            const double lo = sd[C::XLO + j * BB + b], hi = sd[C::XHI + j * BB + b];
+                            a.stage.lo[j * a.stage.cap + k] = lo;
+                            a.stage.mid[j * a.stage.cap + k] = midpoint_rn(lo, hi);
+                            a.stage.hi[j * a.stage.cap + k] = hi;
+                        }
+                        a.stage.sys[k] = sys;
+                        a.stage.meta[k] = (uint32_t)depth & kDepthMask;
+                    } else {
+                        ctl->error = 1;
                     }
-                    a.out.sys[e] = sys;
-                    a.out.flags[e] = flag;
-                    a.out.depth[e] = depth;
-                } else {
-                    atomicOr(stat_ptr(a, sys, ST_FLAGS), (unsigned long long)kFlagResultOverflow);
-                }
-                if (flag == 4) atomicOr(stat_ptr(a, sys, ST_FLAGS), (unsigned long long)kFlagDepthCut);
-            }
-        }
-        // new parents
-        const unsigned ms = __ballot_sync(kFull, fate == 2);
-        if (ms) {
-            unsigned long long pos = 0;
-            if (lane == 0) pos = atomicAdd((unsigned long long *)&ctl->staged, (unsigned long long)__popc(ms));
-            pos = __shfl_sync(kFull, pos, 0);
-            if (fate == 2) {
-                const long long k = (long long)(pos + __popc(ms & lanemask_lt()));
-                if (k < a.stage.cap) {
-#pragma unroll
-                    for (int j = 0; j < N; j++) {
-                        a.stage.lo[j * a.stage.cap + k] = Xlo[j];
-                        a.stage.mid[j * a.stage.cap + k] = xm[j];
-                        a.stage.hi[j * a.stage.cap + k] = Xhi[j];
-                    }
-                    a.stage.sys[k] = sys;
-                    a.stage.meta[k] = (uint32_t)depth & kDepthMask;
-                } else {
-                    ctl->error = 1;
                 }
             }
-        }
-        // statistics (new parents also enter the live count): one atomic per warp when
-        // the warp holds a single system
-        unsigned v[8] = {st_app, st_empty, st_con, st_sing, (fate == 1 && flag != 4) ? 1u : 0u, st_uns,
-                         fate == 2 ? 1u : 0u, fate == 2 ? 1u : 0u};
-        const int slot[8] = {ST_HS_APPLIED, ST_HS_EMPTY, ST_HS_CONTRACTED, ST_HS_SINGULAR, ST_ACCEPTED,
-                             ST_UNSPLITTABLE, ST_SPLIT, ST_LIVE};
-        if (uniform) {
+            // statistics (new parents also enter the live count): one atomic per warp when
+            // the warp holds a single system
+            unsigned v[8] = {st_app, st_empty, st_con, st_sing, (fate == 1 && flag != 4) ? 1u : 0u, st_uns,
+                             fate == 2 ? 1u : 0u, fate == 2 ? 1u : 0u};
+            const int slot[8] = {ST_HS_APPLIED, ST_HS_EMPTY, ST_HS_CONTRACTED, ST_HS_SINGULAR, ST_ACCEPTED,
+                                 ST_UNSPLITTABLE, ST_SPLIT, ST_LIVE};
+            if (uniform) {
 #pragma unroll
-            for (int q = 0; q < 8; q++) {
-                const unsigned tot = __reduce_add_sync(kFull, v[q]);
-                if (lane == 0 && tot) atomicAdd(stat_ptr(a, sys0, slot[q]), (unsigned long long)tot);
+                for (int q = 0; q < 8; q++) {
+                    const unsigned tot = __reduce_add_sync(kFull, v[q]);
+                    if (lane == 0 && tot) atomicAdd(stat_ptr(a, sys0, slot[q]), (unsigned long long)tot);
+                }
+            } else if (active) {
+#pragma unroll
+                for (int q = 0; q < 8; q++)
+                    if (v[q]) atomicAdd(stat_ptr(a, sys, slot[q]), (unsigned long long)v[q]);
             }
-        } else if (active) {
-#pragma unroll
-            for (int q = 0; q < 8; q++)
-                if (v[q]) atomicAdd(stat_ptr(a, sys, slot[q]), (unsigned long long)v[q]);
         }
+        __syncthreads();   // the chunk's arrays and s_base are reused by the next chunk
     }
 }
 
 // ---- launcher -------------------------------------------------------------------
 
-// threads per block: as many (up to 128) as keep the block within ~200 KB of shared memory
-template <int N>
-inline int hs_threads(size_t blob) {
-    const size_t per = hsd::Scratch<N>::BYTES;
-    int t = (int)(((200u * 1024u) - blob) / per);
-    t = (t / 32) * 32;
-    if (t > 128) t = 128;
-    if (t < 32) t = 32;
-    return t;
-}
+// largest dynamic shared memory a block may use (227 KB less the static s_base)
+constexpr size_t kHsSmemLimit = 227 * 1024 - 64;
 
 template <int N>
 static cudaError_t launch_hs_n(const SweepArgs &a, int num_sms, cudaStream_t st) {
+    using C = hsd::Cfg<N>;
     static int per_sm = 0;             // blocks per SM, found once per configuration
     static size_t configured_smem = 0;
-    const size_t blob = a.single ? (size_t)a.blob_smem : 0;
-    const int T = hs_threads<N>(blob);
-    const size_t smem = blob + (size_t)T * hsd::Scratch<N>::BYTES;
+    // cache the term table in shared memory when the plan holds one system and it fits
+    const bool cache = a.single && (size_t)a.blob_smem + C::BYTES <= kHsSmemLimit;
+    const size_t smem = (cache ? (size_t)a.blob_smem : 0) + C::BYTES;
     if (per_sm == 0 || configured_smem != smem) {
         cudaError_t e = cudaFuncSetAttribute(k_hs<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int bl = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, k_hs<N>, T, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, k_hs<N>, C::NT, smem);
         if (e != cudaSuccess) return e;
         per_sm = bl < 1 ? 1 : bl;
         configured_smem = smem;
     }
-    k_hs<N><<<num_sms * per_sm, T, smem, st>>>(a);
+    k_hs<N><<<num_sms * per_sm, C::NT, smem, st>>>(a, cache ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -65,7 +65,11 @@ __device__ __forceinline__ ivd iv_mul(ivd x, ivd y) {
     const double ua = xp ? (yn ? x.lo : x.hi) : (xn ? (yp ? x.hi : x.lo) : (yp ? x.hi : x.lo));
     const double ub = xp ? y.hi : (xn ? y.lo : (yp ? y.hi : y.lo));
     const double ua2 = (xs && ys) ? x.hi : ua, ub2 = (xs && ys) ? y.hi : ub;
-    return {d_min(__dmul_rd(la, lb), __dmul_rd(la2, lb2)), d_max(__dmul_ru(ua, ub), __dmul_ru(ua2, ub2))};
+    const double l1 = __dmul_rd(la, lb), u1 = __dmul_ru(ua, ub);
+    // the second pair only when some lane of the warp has both operands straddling 0
+    // (for the other lanes it repeats the first pair, so their result is unchanged)
+    if (__any_sync(__activemask(), xs && ys)) return {d_min(l1, __dmul_rd(la2, lb2)), d_max(u1, __dmul_ru(ua2, ub2))};
+    return {l1, u1};
 }
 
 // point b times interval y (b a double): two products
@@ -76,6 +80,10 @@ __device__ __forceinline__ ivd iv_smul(double b, ivd y) {
 
 __device__ __forceinline__ double d_abs(double x) {
     return __longlong_as_double(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL);
+}
+// -x by flipping the sign bit (exactly IEEE negation) on the integer pipe
+__device__ __forceinline__ double d_negate(double x) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
 }
 
 // monotone chains for the power rule (argument >= 0)
@@ -91,8 +99,8 @@ __device__ __forceinline__ ivd iv_pow(ivd x, int k) {
     if (k == 1) return x;
     if ((k & 1) == 0) {
         const bool p = !d_neg(x.lo), n = !p && !d_pos(x.hi);
-        const double a = p ? x.lo : (n ? -x.hi : 0.0);
-        const double b = p ? x.hi : (n ? -x.lo : d_max(-x.lo, x.hi));
+        const double a = p ? x.lo : (n ? d_negate(x.hi) : 0.0);
+        const double b = p ? x.hi : (n ? d_negate(x.lo) : d_max(d_negate(x.lo), x.hi));
         return {chain_rd(a, k), chain_ru(b, k)};
     }
     const double al = d_abs(x.lo), ah = d_abs(x.hi);

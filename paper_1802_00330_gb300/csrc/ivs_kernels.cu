@@ -42,8 +42,38 @@ __global__ void __launch_bounds__(kBeginThreads) k_wave_begin(SweepArgs a) {
     __shared__ long long s_first;
     WaveCtl *c = a.ctl;
     const int64_t top = c->top;
-    const int64_t window = top < (int64_t)kBeginThreads * kBeginPer ? top : (int64_t)kBeginThreads * kBeginPer;
     const int t = threadIdx.x;
+    if (a.single) {
+        // one system: every entry has fan-out F = 2^n except the initial box (fan-out 1,
+        // alone in the queue when popped), so the scan below reduces to a closed form
+        if (t != 0) return;
+        int64_t k = 0, children = 0;
+        if (top > 0) {
+            if (a.q.meta[top - 1] & kRootFlag) {
+                k = 1;
+                children = 1;
+            } else {
+                const int64_t F = (int64_t)1 << a.tb.sys[0].n;
+                k = a.wave_children / F;
+                const int64_t by_room = (a.q.cap - top) / (F - 1);
+                k = k < by_room ? k : by_room;
+                k = k < top ? k : top;
+                children = k * F;
+            }
+        }
+        if (k <= 0 && top > 0) c->error = 1;
+        c->base = top - k;
+        c->k = k;
+        c->children = children;
+        c->cursor = 0;
+        c->staged = 0;
+        for (int n = 0; n <= kMaxVars; n++) { c->surv_count[n] = 0; c->hs_cursor[n] = 0; }
+        c->cand_count = 0;
+        c->cand_cursor = 0;
+        c->waves += 1;
+        return;
+    }
+    const int64_t window = top < (int64_t)kBeginThreads * kBeginPer ? top : (int64_t)kBeginThreads * kBeginPer;
     // entry i (0-based from the top) is queue index top - 1 - i
     auto fan_of = [&](int64_t i) -> long long {
         const int64_t e = top - 1 - i;
@@ -164,6 +194,99 @@ __global__ void k_admit(SweepArgs a, const double *box_lo, const double *box_hi,
     if (threadIdx.x == 0) a.ctl->top = top + count;
 }
 
+// ---- purge: drop every queue entry of the cancelled systems ------------------------
+// Serving cancels a request whose time budget ran out; its entries may sit anywhere in
+// the queue.  Compaction without order: the kept entries above the new top move into
+// the holes below it (i-th hole <- i-th kept entry above).  Four launches between
+// sweeps: per-block kept counts, their prefix, hole positions, moves.
+constexpr int kPurgeBlocks = 1024, kPurgeThreads = 256;
+
+// exclusive prefix over the block of v; returns it and leaves the block total in *tot
+__device__ __forceinline__ long long block_excl_scan(long long v, long long *s_warp, long long *tot) {
+    const unsigned lane = lane_id();
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long y = __shfl_up_sync(kFull, x, off);
+        if ((int)lane >= off) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long run = 0;
+        for (int i = 0; i < nw; i++) { const long long t = s_warp[i]; s_warp[i] = run; run += t; }
+        s_warp[nw] = run;
+    }
+    __syncthreads();
+    const long long r = s_warp[w] + x - v;
+    *tot = s_warp[nw];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ bool purge_keep(const SweepArgs &a, const int32_t *cancel, int64_t e) {
+    return cancel[a.q.sys[e]] == 0;
+}
+
+__global__ void __launch_bounds__(kPurgeThreads) k_purge_count(SweepArgs a, const int32_t *cancel, int64_t top,
+                                                               int64_t per, long long *blk) {
+    __shared__ long long s_warp[kPurgeThreads / 32 + 1];
+    const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(b0 + per, top);
+    long long cnt = 0;
+    for (int64_t e = b0 + threadIdx.x; e < b1; e += blockDim.x) cnt += purge_keep(a, cancel, e) ? 1 : 0;
+    long long tot = 0;
+    block_excl_scan(cnt, s_warp, &tot);
+    if (threadIdx.x == 0) blk[blockIdx.x] = tot;
+}
+
+// blk[b] -> kept entries before block b; blk[kPurgeBlocks] = kept total = new top
+__global__ void __launch_bounds__(kPurgeBlocks) k_purge_scan(long long *blk) {
+    __shared__ long long s_warp[kPurgeBlocks / 32 + 1];
+    long long tot = 0;
+    const long long v = blk[threadIdx.x];
+    const long long r = block_excl_scan(v, s_warp, &tot);
+    blk[threadIdx.x] = r;
+    if (threadIdx.x == 0) blk[kPurgeBlocks] = tot;
+}
+
+// pass 0: every hole below the new top K records its position at its rank among those
+// holes, and the thread at K - 1 stores K0 = kept entries below K; pass 1: every kept
+// entry at or above K moves to the hole whose rank is its rank among those entries
+// (kb - K0, kb = kept entries before it); both sets have K - K0 members.  blk[kPurgeBlocks]
+// holds K, blk[kPurgeBlocks + 1] K0.
+__global__ void __launch_bounds__(kPurgeThreads) k_purge_move(SweepArgs a, const int32_t *cancel, int64_t top,
+                                                              int64_t per, long long *blk, uint32_t *hole,
+                                                              int pass, int n_max) {
+    __shared__ long long s_warp[kPurgeThreads / 32 + 1];
+    const long long K = blk[kPurgeBlocks];
+    const long long K0 = pass == 1 ? blk[kPurgeBlocks + 1] : 0;
+    const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(b0 + per, top);
+    long long before = blk[blockIdx.x];   // kept entries in [0, tile start)
+    for (int64_t t0 = b0; t0 < b1; t0 += blockDim.x) {
+        const int64_t e = t0 + threadIdx.x;
+        const bool in = e < b1;
+        const bool keep = in && purge_keep(a, cancel, e);
+        long long tot = 0;
+        const long long kb = before + block_excl_scan(keep ? 1 : 0, s_warp, &tot);   // kept in [0, e)
+        if (in && pass == 0) {
+            if (!keep && e < K) hole[e - kb] = (uint32_t)e;   // holes in [0, e) = e - kb
+            if (e == K - 1) blk[kPurgeBlocks + 1] = kb + (keep ? 1 : 0);
+        } else if (in && pass == 1 && keep && e >= K) {
+            const int64_t d = hole[kb - K0];
+            for (int j = 0; j < n_max; j++) {
+                a.q.lo[j * a.q.cap + d] = a.q.lo[j * a.q.cap + e];
+                a.q.mid[j * a.q.cap + d] = a.q.mid[j * a.q.cap + e];
+                a.q.hi[j * a.q.cap + d] = a.q.hi[j * a.q.cap + e];
+            }
+            a.q.sys[d] = a.q.sys[e];
+            a.q.meta[d] = a.q.meta[e];
+        }
+        before += tot;
+    }
+    if (pass == 1 && blockIdx.x == 0 && threadIdx.x == 0) a.ctl->top = K;
+}
+
 __global__ void k_loop_cond(SweepArgs a, cudaGraphConditionalHandle h) {
     if (threadIdx.x != 0) return;
     const WaveCtl *c = a.ctl;
@@ -247,6 +370,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(SweepArgs a) {
     const int w = threadIdx.x >> 5;
     WaveCtl *ctl = a.ctl;
     const int64_t base = ctl->base, K = ctl->k;
+    // blocks beyond what K parents need leave at once (the others take every parent
+    // from the shared cursor), so a small sweep does not pay for the whole grid
+    if ((int64_t)blockIdx.x * (blockDim.x >> 5) >= K) return;
     if (a.single) {
         const DevSys &S0 = a.tb.sys[0];
         copy_blob(s_blob, a.tb.blobs + S0.blob_off, (uint32_t)S0.blob_bytes);
@@ -370,7 +496,7 @@ __global__ void __launch_bounds__(kEval64Threads) k_eval64(SweepArgs a) {
     double *X = sX + tid;
     WaveCtl *ctl = a.ctl;
     const int64_t count = ctl->cand_count;
-    if (count == 0) return;
+    if ((int64_t)blockIdx.x * blockDim.x >= count) return;   // not needed for this many candidates
     if (a.single) {
         const DevSys &S0 = a.tb.sys[0];
         copy_blob(s_blob, a.tb.blobs + S0.blob_off, (uint32_t)S0.blob_bytes);
@@ -523,6 +649,17 @@ cudaError_t build_sweep_graph(const SweepArgs &a, const int *hs_dims, int n_hs_d
 cudaError_t launch_admit(const SweepArgs &a, const double *d_lo, const double *d_hi, const int32_t *d_slot,
                          const int32_t *d_depth, int count, int n_max, cudaStream_t st) {
     k_admit<<<1, 256, 0, st>>>(a, d_lo, d_hi, d_slot, d_depth, count, n_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_purge(const SweepArgs &a, const int32_t *d_cancel, int64_t top, int n_max, long long *d_blk,
+                         uint32_t *d_hole, cudaStream_t st) {
+    if (top <= 0) return cudaSuccess;
+    const int64_t per = (top + kPurgeBlocks - 1) / kPurgeBlocks;
+    k_purge_count<<<kPurgeBlocks, kPurgeThreads, 0, st>>>(a, d_cancel, top, per, d_blk);
+    k_purge_scan<<<1, kPurgeBlocks, 0, st>>>(d_blk);
+    k_purge_move<<<kPurgeBlocks, kPurgeThreads, 0, st>>>(a, d_cancel, top, per, d_blk, d_hole, 0, n_max);
+    k_purge_move<<<kPurgeBlocks, kPurgeThreads, 0, st>>>(a, d_cancel, top, per, d_blk, d_hole, 1, n_max);
     return cudaGetLastError();
 }
 

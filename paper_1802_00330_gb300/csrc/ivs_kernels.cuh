@@ -63,6 +63,12 @@ cudaError_t launch_seed_roots(const SweepArgs &a, const double *d_box_lo, const 
 // appends initial boxes of newly admitted systems (slot ids) on top of the queue
 cudaError_t launch_admit(const SweepArgs &a, const double *d_lo, const double *d_hi, const int32_t *d_slot,
                          const int32_t *d_depth, int count, int n_max, cudaStream_t st);
+// Serving: removes every queue entry whose system has d_cancel[sys] != 0 (between
+// sweeps; `top` = the current queue size).  d_blk: kPurgeScratch long longs;
+// d_hole: `top` uint32 entries.  Sets ctl->top to the entries left.
+constexpr int kPurgeScratch = 1024 + 2;
+cudaError_t launch_purge(const SweepArgs &a, const int32_t *d_cancel, int64_t top, int n_max, long long *d_blk,
+                         uint32_t *d_hole, cudaStream_t st);
 // Hansen-Sengupta + accept/split kernel for dimension n (ivs_hs_*.cu)
 cudaError_t launch_hs_dim1(const SweepArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_hs_dim2(const SweepArgs &a, int num_sms, cudaStream_t st);

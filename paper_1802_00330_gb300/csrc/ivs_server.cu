@@ -86,6 +86,9 @@ struct ivs_server {
     int32_t *h_rslot = nullptr, *h_rdepth = nullptr;
     double *d_rlo = nullptr, *d_rhi = nullptr;
     int32_t *d_rslot = nullptr, *d_rdepth = nullptr;
+    int32_t *d_cancel = nullptr;                   // per slot: 1 = its queue entries are purged
+    long long *d_pblk = nullptr;                   // purge scratch
+    uint32_t *d_hole = nullptr;                    // purge hole positions (queue capacity)
     int64_t q_cap = 0, rps = 0, reserved = 0;
     std::vector<Slot> slots;
     std::vector<int> free_slots;
@@ -121,6 +124,7 @@ ivs_server::~ivs_server() {
     if (graph) cudaGraphDestroy(graph);
     if (ws) cudaFree(ws);
     if (tables) cudaFree(tables);
+    if (d_hole) cudaFree(d_hole);
     if (h_ctl) cudaFreeHost(h_ctl);
     if (h_stats) cudaFreeHost(h_stats);
     if (h_limit) cudaFreeHost(h_limit);
@@ -165,15 +169,21 @@ int ivs_server::init() {
     // and depths) in a second allocation
     const size_t sys_bytes = align_up((size_t)S * sizeof(DevSys), 256);
     const size_t blob_bytes = (size_t)S * kBlobSlot;
-    const size_t adm_bytes = (size_t)S * (2 * (size_t)n_max * sizeof(double) + 2 * sizeof(int32_t));
-    CUDA_TRY(cudaMalloc(&tables, sys_bytes + blob_bytes + adm_bytes));
-    CUDA_TRY(cudaMemsetAsync(tables, 0, sys_bytes, stream));
+    const size_t adm_bytes = align_up((size_t)S * (2 * (size_t)n_max * sizeof(double) + 2 * sizeof(int32_t)), 256);
+    const size_t purge_bytes = (size_t)kPurgeScratch * sizeof(long long) + (size_t)S * sizeof(int32_t);
+    CUDA_TRY(cudaMalloc(&tables, sys_bytes + blob_bytes + adm_bytes + purge_bytes));
+    CUDA_TRY(cudaMemsetAsync(tables, 0, sys_bytes + blob_bytes + adm_bytes + purge_bytes, stream));
     d_sys = (DevSys *)tables;
     d_blobs = (char *)tables + sys_bytes;
     d_rlo = (double *)(d_blobs + blob_bytes);
     d_rhi = d_rlo + (size_t)S * n_max;
     d_rslot = (int32_t *)(d_rhi + (size_t)S * n_max);
     d_rdepth = d_rslot + S;
+    d_pblk = (long long *)(d_blobs + blob_bytes + adm_bytes);
+    d_cancel = (int32_t *)(d_pblk + kPurgeScratch);
+    if (q_cap > (int64_t)0xFFFFFFFFLL) return fail(IVS_ERR_INVALID, "server queue above 2^32 entries");
+    e = cudaMalloc(&d_hole, (size_t)q_cap * sizeof(uint32_t));
+    if (e != cudaSuccess) return fail(IVS_ERR_NOMEM, std::string("cudaMalloc purge buffer: ") + cudaGetErrorString(e));
     a.tb.sys = d_sys;
     a.tb.blobs = d_blobs;
     CUDA_TRY(cudaMallocHost((void **)&h_ctl, sizeof(WaveCtl)));
@@ -216,6 +226,23 @@ void ivs_server::fail_all_active(int status, std::vector<std::pair<uint64_t, ivs
 
 // One step: admit, run sweeps, collect finished systems.  Returns a CUDA status.
 int ivs_server::step(std::vector<std::pair<uint64_t, ivs_result *>> &finished) {
+    // (1) requests past their time budget leave the queue at once: their entries are
+    // purged wherever they sit, and they complete in this step (IVS_ERR_TIMEOUT)
+    {
+        const auto now0 = Clock::now();
+        bool any = false;
+        for (int s = 0; s < (int)slots.size(); s++) {
+            Slot &sl = slots[s];
+            if (!sl.used || sl.cancelled || !(sl.req.opt.time_budget_s > 0)) continue;
+            if (std::chrono::duration<double>(now0 - sl.req.t_admit).count() <= sl.req.opt.time_budget_s) continue;
+            sl.cancelled = true;
+            any = true;
+            CUDA_TRY(cudaMemsetAsync(d_cancel + s, 0x01, sizeof(int32_t), stream));
+            CUDA_TRY(cudaMemsetAsync(a.stats + (size_t)s * ST_COUNT + ST_LIVE, 0, sizeof(unsigned long long), stream));
+        }
+        if (any) CUDA_TRY(launch_purge(a, d_cancel, h_ctl->top, n_max, d_pblk, d_hole, stream));
+    }
+    // (2) admission
     std::vector<Request> admit;
     std::vector<int> admit_slot;
     {
@@ -253,6 +280,7 @@ int ivs_server::step(std::vector<std::pair<uint64_t, ivs_result *>> &finished) {
         CUDA_TRY(cudaMemcpyAsync(d_sys + s, &d, sizeof(DevSys), cudaMemcpyHostToDevice, stream));
         CUDA_TRY(cudaMemcpyAsync(d_blobs + d.blob_off, h.blobs.data(), h.blobs.size(), cudaMemcpyHostToDevice, stream));
         CUDA_TRY(cudaMemsetAsync(a.stats + (size_t)s * ST_COUNT, 0, ST_COUNT * sizeof(unsigned long long), stream));
+        CUDA_TRY(cudaMemsetAsync(d_cancel + s, 0, sizeof(int32_t), stream));
         for (int j = 0; j < n_max; j++) {
             h_rlo[(size_t)n_adm * n_max + j] = j < rq.n ? rq.lo[j] : 0.0;
             h_rhi[(size_t)n_adm * n_max + j] = j < rq.n ? rq.hi[j] : 0.0;
@@ -277,18 +305,7 @@ int ivs_server::step(std::vector<std::pair<uint64_t, ivs_result *>> &finished) {
         stats.admitted += n_adm;
     }
     if (active == 0) return IVS_OK;
-    // per-request time budgets: a late system gets a box budget of 1, so the next sweep
-    // drops its remaining boxes and it completes (reported as IVS_ERR_TIMEOUT)
-    const auto now0 = Clock::now();
-    for (int s = 0; s < (int)slots.size(); s++) {
-        Slot &sl = slots[s];
-        if (!sl.used || sl.cancelled || !(sl.req.opt.time_budget_s > 0)) continue;
-        if (std::chrono::duration<double>(now0 - sl.req.t_admit).count() <= sl.req.opt.time_budget_s) continue;
-        sl.cancelled = true;
-        sl.dev.max_boxes = 1;
-        CUDA_TRY(cudaMemcpyAsync(d_sys + s, &sl.dev, sizeof(DevSys), cudaMemcpyHostToDevice, stream));
-    }
-    // a few sweeps through the sweep graph
+    // (3) a few sweeps through the sweep graph
     const int64_t waves0 = h_ctl->waves;
     *h_limit = waves0 + cfg.sweeps_per_step;
     CUDA_TRY(cudaMemcpyAsync(&a.ctl->wave_limit, h_limit, sizeof(int64_t), cudaMemcpyHostToDevice, stream));

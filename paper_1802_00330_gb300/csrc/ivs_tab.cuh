@@ -40,12 +40,19 @@ __host__ __device__ inline BlobLayout blob_layout(int T, int P, int F, int TF = 
     return L;
 }
 
+// term info word: factor start << 5 | factor count, and bit 31 set when the coefficient
+// interval is a point (c_lo == c_hi), which lets the FP64 product take two multiplies
+// instead of a general interval product (the same numbers either way)
+constexpr uint32_t kTermPoint = 1u << 31;
+__host__ __device__ inline int term_nf(uint32_t info) { return (int)(info & 31u); }
+__host__ __device__ inline int term_f0(uint32_t info) { return (int)((info & ~kTermPoint) >> 5); }
+
 struct SysTab {
     const float4 *cs;        // {rd32(c_lo), ru32(c_lo), rd32(c_hi), ru32(c_hi)}
     const double *clo, *chi; // coefficient interval
     const float *clo32, *chi32;
     const int32_t *poly_off; // [P + 1] term ranges
-    const uint32_t *tinfo;   // factor start << 5 | factor count
+    const uint32_t *tinfo;   // term info words (above)
     const int32_t *tv_off;   // [TF + 1]: first combination entry of each F term
     const uint32_t *tv_map;  // [E]: term << 8 | combination of its variables' halves
     const uint8_t *fac;
@@ -77,29 +84,28 @@ __device__ __forceinline__ void copy_blob(char *dst, const char *src, uint32_t b
 // ---- evaluators over a coordinate accessor x(j) ----------------------------------------
 
 template <class Coord>
+__device__ __forceinline__ ivd term64(const SysTab &T, int t, const Coord &x) {
+    const ivd cf = {T.clo[t], T.chi[t]};
+    const uint32_t info = T.tinfo[t];
+    const int nf = term_nf(info), f0 = term_f0(info);
+    if (nf == 0) return cf;
+    unsigned fc = T.fac[f0];
+    ivd prod = iv_pow(x(fc >> 4), (int)(fc & 15u));
+    for (int f = 1; f < nf; f++) {
+        fc = T.fac[f0 + f];
+        prod = iv_mul(prod, iv_pow(x(fc >> 4), (int)(fc & 15u)));
+    }
+    // a point coefficient c: [c,c] * prod equals c * prod (two products, not four);
+    // the flag is the term's, so the lanes of a warp take the same branch
+    return (info & kTermPoint) ? iv_smul(cf.lo, prod) : iv_mul(cf, prod);
+}
+
+template <class Coord>
 __device__ __forceinline__ ivd poly64(const SysTab &T, int p, const Coord &x) {
     const int t0 = T.poly_off[p], t1 = T.poly_off[p + 1];
-    ivd acc = {0.0, 0.0};
-    for (int t = t0; t < t1; t++) {
-        const ivd cf = {T.clo[t], T.chi[t]};
-        const uint32_t info = T.tinfo[t];
-        const int nf = (int)(info & 31u), f0 = (int)(info >> 5);
-        ivd v;
-        if (nf == 0) {
-            v = cf;
-        } else {
-            unsigned fc = T.fac[f0];
-            ivd prod = iv_pow(x(fc >> 4), (int)(fc & 15u));
-            for (int f = 1; f < nf; f++) {
-                fc = T.fac[f0 + f];
-                prod = iv_mul(prod, iv_pow(x(fc >> 4), (int)(fc & 15u)));
-            }
-            // a point coefficient c: [c,c] * prod equals c * prod (two products, not four);
-            // every lane evaluates the same term, so the test does not diverge
-            v = (cf.lo == cf.hi) ? iv_smul(cf.lo, prod) : iv_mul(cf, prod);
-        }
-        acc = (t == t0) ? v : iv_add(acc, v);
-    }
+    if (t0 == t1) return ivd{0.0, 0.0};
+    ivd acc = term64(T, t0, x);
+    for (int t = t0 + 1; t < t1; t++) acc = iv_add(acc, term64(T, t, x));
     return acc;
 }
 
@@ -110,7 +116,7 @@ __device__ __forceinline__ ivf poly32(const SysTab &T, int p, const Coord &x) {
     for (int t = t0; t < t1; t++) {
         const ivf cf = {T.clo32[t], T.chi32[t]};
         const uint32_t info = T.tinfo[t];
-        const int nf = (int)(info & 31u), f0 = (int)(info >> 5);
+        const int nf = term_nf(info), f0 = term_f0(info);
         ivf v;
         if (nf == 0) {
             v = cf;
@@ -136,7 +142,7 @@ __device__ __forceinline__ shv poly_shadow(const SysTab &T, int p, const Coord &
         const float4 ce = T.cs[t];
         const shv cf = {ce.x, ce.y, ce.z, ce.w};
         const uint32_t info = T.tinfo[t];
-        const int nf = (int)(info & 31u), f0 = (int)(info >> 5);
+        const int nf = term_nf(info), f0 = term_f0(info);
         shv v;
         if (nf == 0) {
             v = cf;
@@ -196,7 +202,7 @@ template <class Coord>
 __device__ __forceinline__ float4 term_shadow(const SysTab &T, int t, const Coord &x) {
     const float4 ce = T.cs[t];
     const uint32_t info = T.tinfo[t];
-    const int nf = (int)(info & 31u), f0 = (int)(info >> 5);
+    const int nf = term_nf(info), f0 = term_f0(info);
     if (nf == 0) return ce;
     bool poison = false;
     unsigned fc = T.fac[f0];
@@ -222,7 +228,7 @@ __device__ __forceinline__ int decide_from_table(const SysTab &T, const DevSys &
         shv acc = {0.f, 0.f, 0.f, 0.f};
         for (int t = t0; t < t1; t++) {
             const uint32_t info = T.tinfo[t];
-            const int nf = (int)(info & 31u), f0 = (int)(info >> 5);
+            const int nf = term_nf(info), f0 = term_f0(info);
             unsigned q = 0;
             for (int f = 0; f < nf; f++) q |= ((c >> (T.fac[f0 + f] >> 4)) & 1u) << f;
             const float4 v = tv[T.tv_off[t] + (int)q];

@@ -119,3 +119,29 @@ def test_many_slots_and_a_large_admission_burst(B):
         assert all(r["status"] == 0 for r in results)
     finally:
         sv.close()
+
+
+def test_time_budget_frees_the_queue(B):
+    """A request that runs out of its time budget completes with IVS_ERR_TIMEOUT soon
+    after the budget, its queue entries are purged, and the requests sharing the queue
+    with it still finish with exact results."""
+    hard = synth.config_n10()
+    small = synth.config_batched(count=12, seed=99, n_range=(2, 4))
+    sv = B.Server(workspace_bytes=1 << 31, max_slots=32, wave_children=1 << 20, max_vars=10)
+    try:
+        t0 = time.time()
+        th = sv.submit(hard, time_budget_s=0.3)
+        ts = [sv.submit(s) for s in small]
+        r_hard = wait_all(sv, [th], budget_s=60.0)[0]
+        assert r_hard["status"] == 4                       # IVS_ERR_TIMEOUT
+        assert time.time() - t0 < 10.0
+        res = wait_all(sv, ts)
+        for s, r in zip(small, res):
+            assert same(r, B.solve(s))
+        st = sv.stats()
+        assert st["last_error"] == "" and st["in_flight"] == 0
+        # the server keeps working after the purge
+        again = wait_all(sv, [sv.submit(small[0])])[0]
+        assert same(again, res[0])
+    finally:
+        sv.close()
