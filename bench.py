@@ -86,6 +86,30 @@ def hs_ops(s):
             + 4 * n * n - 2 * n + n * (6 * (n - 1) + 4) + 2 * n)
 
 
+# ---- measured DRAM traffic of the dominant kernel ----------------------------------------
+# ncu's dram__bytes_read.sum + dram__bytes_write.sum per k_hs<6> launch, averaged over the
+# 10 launches of one n=6 solve (profiles/k_hs_n6_dram.md).  Valid only for the kernel sources
+# it was taken with: the bench reports null once their hash differs.
+HS_TRAFFIC_N6 = {"sources_sha256": None, "bytes_per_launch": None}
+HS_SOURCES = ("ivs_hs.cuh", "ivs_tab.cuh", "ivs_interval.cuh", "ivs_internal.h", "ivs_kernels.cuh")
+
+
+def hs_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1802_00330_gb300", "csrc")
+    for f in HS_SOURCES:
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def hs_traffic(workload, kernel):
+    if workload != "n6" or kernel != "hs_n6" or HS_TRAFFIC_N6["sources_sha256"] != hs_sources_sha():
+        return None
+    return HS_TRAFFIC_N6["bytes_per_launch"]
+
+
 # ---- multi-rank aggregation ----------------------------------------------------------
 def reduce_over_ranks(t_dev, boxes, device="cpu"):
     """Whole-job numbers over the ranks of the default process group: the slowest
@@ -342,8 +366,10 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
         work = "control kernels"
     achieved = ops / (dom[1][1] * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": dom[0], "achieved": achieved, "peak": fp64_rate / 1e12,
-                "unit": "TFLOP/s (FP64 directed ops)", "frac": achieved / (fp64_rate / 1e12),
-                "traffic": None, "peak_source": "measured in this run: directed __dadd_rd/__dmul_ru probe",
+                "unit": "TFLOP/s", "frac": achieved / (fp64_rate / 1e12),
+                "traffic": hs_traffic(args.workload, dom[0]),
+                "op_convention": "one directed FP64 add or multiply = 1 flop (no FMA on the path)",
+                "peak_source": "measured in this run: directed __dadd_rd/__dmul_ru probe",
                 "work": work, "kernel_share": dom[1][1] / sum(v[1] for v in ktimes.values()),
                 "avg_launch_ms": dom[1][1] / max(1, dom[1][0])}
 
