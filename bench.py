@@ -176,12 +176,12 @@ class ClockSampler:
 
 
 # ---- the oracle as CPU baseline / reference arm ---------------------------------------
-def oracle_sample(systems, budget_boxes):
+def oracle_sample(systems, budget_boxes, centred=False):
     import oracle
     t = time.perf_counter()
     boxes = 0
     for s in systems:
-        r = oracle.solve(s, max_boxes=budget_boxes)
+        r = oracle.solve(s, max_boxes=budget_boxes, centred=centred)
         boxes += r["stats"]["boxes"]
         if time.perf_counter() - t > 60:
             break
@@ -194,10 +194,10 @@ def run_reference(args, systems, desc, rank, world):
         return
     budget = args.ref_boxes
     for _ in range(args.warmup):
-        oracle_sample(systems[:1], budget // 10)
+        oracle_sample(systems[:1], budget // 10, args.centred)
     tot_b, tot_t = 0, 0.0
     for _ in range(args.steps):
-        b, t = oracle_sample(systems[:1], budget)
+        b, t = oracle_sample(systems[:1], budget, args.centred)
         tot_b += b
         tot_t += t
     v = tot_b / tot_t
@@ -227,7 +227,8 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
         # batching form: the autotuner picks the sweep size and evaluation grid (outside timing)
         tuned = B.autotune(systems[: min(len(systems), 256)], trial_boxes=100_000)
         args.wave_children = int(tuned["wave_children"])
-    plan = B.Plan(systems, stream=stream, wave_children=args.wave_children,
+    base_opts = {"centred_form": 1} if args.centred else {}
+    plan = B.Plan(systems, opts=base_opts or None, stream=stream, wave_children=args.wave_children,
                   eval_blocks=(tuned or {}).get("eval_blocks", 0))       # graph path
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
 
@@ -286,7 +287,8 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
     assert np.array_equal(res["lo"], ref["lo"]) and np.array_equal(res["hi"], ref["hi"])
 
     # plain FP64 path (prefilter off) on the same workload, same GPU
-    plan64 = B.Plan(systems, opts={"prefilter_fp32": 0}, stream=stream, wave_children=args.wave_children)
+    plan64 = B.Plan(systems, opts={**base_opts, "prefilter_fp32": 0}, stream=stream,
+                    wave_children=args.wave_children)
     for _ in range(2):
         plan64.run()
     t64 = []
@@ -316,14 +318,14 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
     if len(systems) == 1:
         for _ in range(args.steps):
             t0 = time.perf_counter()
-            r = B.solve(s0)
+            r = B.solve(s0, **base_opts)
             e2e_t.append(time.perf_counter() - t0)
             e2e_boxes += r["stats"]["boxes"]
             d2h = r["lo"].nbytes + r["hi"].nbytes + r["flags"].nbytes + r["depth"].nbytes
     else:
         for _ in range(max(1, args.steps // 2)):
             t0 = time.perf_counter()
-            outs = B.solve_batch(systems)
+            outs = B.solve_batch(systems, **base_opts)
             e2e_t.append(time.perf_counter() - t0)
             e2e_boxes += sum(o["stats"]["boxes"] for o in outs)
     e2e = {"value": e2e_boxes / float(np.sum(e2e_t)), "unit": "boxes/s", "h2d_bytes_per_step": int(h2d),
@@ -331,7 +333,7 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
 
     # per-kernel device time: the same solve through the host loop with CUDA events
     # around every stage (a graph body cannot hold event nodes), over the same K steps
-    prof = B.Plan(systems, stream=stream, profile=True, wave_children=args.wave_children)
+    prof = B.Plan(systems, opts=base_opts or None, stream=stream, profile=True, wave_children=args.wave_children)
     prof.run()
     ktimes = {}
     prof_boxes = 0
@@ -377,7 +379,7 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            b, t = oracle_sample(systems[:1], args.cpu_boxes)
+            b, t = oracle_sample(systems[:1], args.cpu_boxes, args.centred)
             cpu = {"value": b / t, "unit": "boxes/s", "cores": 1, "kind": "oracle",
                    "sample": f"first {b} boxes (LIFO order) of the {args.workload} solve, serial, fesetround"}
         out = {
@@ -486,6 +488,8 @@ def main():
     ap.add_argument("--served-budget", type=float, default=2.0)
     ap.add_argument("--served-workspace", type=int, default=16, help="GiB")
     ap.add_argument("--batched-count", type=int, default=4096)
+    ap.add_argument("--centred", action="store_true",
+                    help="add the centred-form exclusion test before Hansen-Sengupta")
     ap.add_argument("--only-timed", action="store_true",
                     help="time the device-resident solve only (for profiler runs)")
     args = ap.parse_args()
@@ -501,6 +505,8 @@ def main():
             "int coef [-5,5], planted roots, box [-4,4]^n, tol 1e-6")
     else:
         systems, desc = workload(args.workload)
+    if args.centred:
+        desc += ", centred-form exclusion before HS"
     if args.impl == "reference":
         run_reference(args, systems, desc, rank, world)
         return

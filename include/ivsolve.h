@@ -82,6 +82,12 @@ typedef struct ivs_options {
     int64_t max_boxes;       /* work budget in processed boxes, 0 = unlimited          */
     int64_t max_results;     /* accepted-box capacity, 0 = library default             */
     double time_budget_s;    /* wall-clock budget, 0 = unlimited                       */
+    int32_t centred_form;    /* 1: after the natural form, a second exclusion test by
+                                the centred (mean-value) form from the expansion of
+                                Section 2.3 eq 13, F_c,i(X) = f_i(x) + sum_j J_ij(X)
+                                (X_j - x_j) at x = mid X, folded over j = 1..n; a box
+                                is dropped when some F_c,i(X) excludes 0.  Needs
+                                n_eqs == n_vars.  0 (default): natural form only.       */
 } ivs_options;
 
 typedef struct ivs_stats {
@@ -103,6 +109,7 @@ typedef struct ivs_stats {
     int64_t kept_shadow;        /* boxes the FP32 shadow proved FP64 would keep        */
     double queue_ms;            /* served requests: submit -> admission                */
     double solve_ms;            /* served requests: admission -> result ready          */
+    int64_t excluded_centred;   /* dropped by the centred form (centred_form = 1)      */
 } ivs_stats;
 
 typedef struct ivs_result ivs_result;

@@ -48,14 +48,15 @@ class _Sys(C.Structure):
 class _Opt(C.Structure):
     _fields_ = [("tol", C.c_double), ("hs_enable", C.c_int32), ("hs_min_depth", C.c_int32),
                 ("hs_iters", C.c_int32), ("root_depth", C.c_int32), ("max_depth", C.c_int32),
-                ("order", C.c_int32), ("order_seed", C.c_uint64), ("max_boxes", C.c_int64)]
+                ("order", C.c_int32), ("order_seed", C.c_uint64), ("max_boxes", C.c_int64),
+                ("centred", C.c_int32)]
 
 
 class _Stats(C.Structure):
     _fields_ = [("boxes", C.c_int64), ("excluded_eval", C.c_int64), ("hs_applied", C.c_int64),
                 ("hs_empty", C.c_int64), ("hs_contracted", C.c_int64), ("hs_singular", C.c_int64),
                 ("accepted", C.c_int64), ("unsplittable", C.c_int64), ("split", C.c_int64),
-                ("max_depth_seen", C.c_int32)]
+                ("max_depth_seen", C.c_int32), ("excluded_centred", C.c_int64)]
 
 
 def _load():
@@ -82,6 +83,7 @@ def _load():
             lib.orc_jacobian.argtypes = [C.POINTER(_Sys), vp, vp, vp, vp]
             lib.orc_gj_inverse.argtypes = [C.c_int, vp, vp]
             lib.orc_hs_step.argtypes = [C.POINTER(_Sys), vp, vp, vp, vp]
+            lib.orc_centred.argtypes = [C.POINTER(_Sys), vp, vp, vp, vp]
             _lib = lib
     return _lib
 
@@ -103,7 +105,7 @@ class _SysHolder:
 
 
 def solve(s, box_lo=None, box_hi=None, tol=None, hs_enable=True, hs_min_depth=0, hs_iters=1,
-          root_depth=0, max_depth=200, order=0, order_seed=0, max_boxes=0):
+          root_depth=0, max_depth=200, order=0, order_seed=0, max_boxes=0, centred=False):
     """Run the serial solver.  Returns a dict with sorted boxes, flags, depths, stats, status."""
     lib = _load()
     h = _SysHolder(s)
@@ -111,7 +113,7 @@ def solve(s, box_lo=None, box_hi=None, tol=None, hs_enable=True, hs_min_depth=0,
     hi = np.ascontiguousarray(s.box_hi if box_hi is None else box_hi, dtype=np.float64)
     opt = _Opt(float(s.tol if tol is None else tol), int(hs_enable), int(hs_min_depth),
                int(hs_iters), int(root_depth), int(max_depth), int(order), int(order_seed),
-               int(max_boxes))
+               int(max_boxes), int(bool(centred)))
     res = C.c_void_p()
     lib.orc_solve(C.byref(h.c), _ptr(lo), _ptr(hi), C.byref(opt), C.byref(res))
     try:
@@ -210,3 +212,16 @@ def hs_step(s, lo, hi):
     oh = hi.copy()
     rc = lib.orc_hs_step(C.byref(h.c), _ptr(lo), _ptr(hi), _ptr(ol), _ptr(oh))
     return rc, ol, oh
+
+
+def centred(s, lo, hi):
+    """Centred form F_c,i(X) = f_i(mid X) + sum_j J_ij(X) (X_j - mid X_j) of every
+    equation (n_eqs == n_vars); returns (lo, hi) arrays."""
+    lib = _load()
+    h = _SysHolder(s)
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    ol = np.zeros(s.n_eqs)
+    oh = np.zeros(s.n_eqs)
+    lib.orc_centred(C.byref(h.c), _ptr(lo), _ptr(hi), _ptr(ol), _ptr(oh))
+    return ol, oh

@@ -276,6 +276,32 @@ static double midpoint(double lo, double hi) { return 0.5 * (lo + hi); }  /* eq 
  * r wrong and drops its index; eq 21 is followed.  When Y_i has two pieces X'_i is the
  * hull of the two intersections.  A NaN in S_i or M_ii leaves X'_i = X_i.
  * Returns 0 (out written), 1 (empty), 2 (skipped: mid(J) singular or B non-finite). */
+/* Centred (mean-value) form.  Section 2.3 eq 13 expands f about the point x:
+ * f(y) = f(x) + J(xi)(y - x) with xi in X, so for every y in X and x = mid X,
+ * f_i(y) lies in F_c,i(X) = f_i(x) + sum_j J_ij(X) (X_j - x_j).  Computed with the same
+ * J(X), the same thin-box f(x) at the RN midpoint and the same outward operations as the
+ * Hansen-Sengupta step; the sum is a left fold over j = 1..n starting from f_i(x). */
+static void centred_form(const orc_system *s, const ivl *X, ivl *Fc) {
+    int n = s->n_vars;
+    size_t nn = (size_t)n * (size_t)n;
+    ivl *J = (ivl *)malloc(sizeof(ivl) * nn);
+    ivl *xc = (ivl *)malloc(sizeof(ivl) * (size_t)n);
+    ivl *fx = (ivl *)malloc(sizeof(ivl) * (size_t)n);
+    if (!J || !xc || !fx) {
+        for (int i = 0; i < n; i++) { Fc[i].lo = -INFINITY; Fc[i].hi = INFINITY; }
+    } else {
+        jacobian(s, X, J);
+        for (int j = 0; j < n; j++) { double m = midpoint(X[j].lo, X[j].hi); xc[j].lo = m; xc[j].hi = m; }
+        eval_system(s, xc, fx);
+        for (int i = 0; i < n; i++) {
+            ivl acc = fx[i];
+            for (int j = 0; j < n; j++) acc = iv_add(acc, iv_mul(J[i * n + j], iv_sub(X[j], xc[j])));
+            Fc[i] = acc;
+        }
+    }
+    free(J); free(xc); free(fx);
+}
+
 static int hs_sweep(const orc_system *s, const ivl *X, ivl *Xo) {
     int n = s->n_vars;
     size_t nn = (size_t)n * (size_t)n;
@@ -423,7 +449,7 @@ static int validate(const orc_system *s, const double *lo, const double *hi, con
         for (int j = 0; j < s->n_vars; j++) if (s->exps[(size_t)t * s->n_vars + j] > 15) return 1;
     }
     for (int j = 0; j < s->n_vars; j++) if (!isfinite(lo[j]) || !isfinite(hi[j]) || lo[j] > hi[j]) return 1;
-    if (o->hs_enable && s->n_eqs != s->n_vars) return 1;
+    if ((o->hs_enable || o->centred) && s->n_eqs != s->n_vars) return 1;
     if (!(o->tol >= 0) || !isfinite(o->tol) || o->hs_iters < 0 || o->max_depth < 0) return 1;
     return 0;
 }
@@ -500,6 +526,12 @@ int orc_solve(const orc_system *s, const double *box_lo, const double *box_hi,
         /* Algorithm 2, last step / Definition 2: drop boxes where some F_i excludes 0 */
         eval_system(s, X, F);
         if (excluded(F, m)) { res->st.excluded_eval++; continue; }
+
+        /* optional second exclusion test: the centred form (eq 13) */
+        if (o->centred) {
+            centred_form(s, X, F);
+            if (excluded(F, m)) { res->st.excluded_centred++; continue; }
+        }
 
         /* Algorithm 1 step (III): Hansen-Sengupta contraction */
         if (o->hs_enable && depth >= o->hs_min_depth) {
@@ -656,6 +688,18 @@ void orc_jacobian(const orc_system *s, const double *lo, const double *hi, doubl
 }
 
 int orc_gj_inverse(int n, const double *a, double *inv) { return gj_inverse(n, a, inv); }
+
+void orc_centred(const orc_system *s, const double *lo, const double *hi, double *out_lo, double *out_hi) {
+    int n = s->n_vars;
+    ivl *X = (ivl *)malloc(sizeof(ivl) * (size_t)n);
+    ivl *F = (ivl *)malloc(sizeof(ivl) * (size_t)n);
+    if (X && F) {
+        for (int j = 0; j < n; j++) { X[j].lo = lo[j]; X[j].hi = hi[j]; }
+        centred_form(s, X, F);
+        for (int i = 0; i < n; i++) { out_lo[i] = F[i].lo; out_hi[i] = F[i].hi; }
+    }
+    free(X); free(F);
+}
 
 int orc_hs_step(const orc_system *s, const double *lo, const double *hi, double *out_lo, double *out_hi) {
     ivl X[16], Xo[16];

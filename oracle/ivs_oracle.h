@@ -39,6 +39,8 @@ typedef struct {
     int32_t order;          /* 0 LIFO, 1 FIFO, 2 seeded random pop                  */
     uint64_t order_seed;
     int64_t max_boxes;      /* work budget: boxes processed (0 = unlimited)         */
+    int32_t centred;        /* 1: after the natural form, drop boxes whose centred
+                               (mean-value) form excludes 0 (needs n_eqs == n_vars)  */
 } orc_options;
 
 /* result flags per accepted box */
@@ -63,6 +65,7 @@ typedef struct {
     int64_t unsplittable;
     int64_t split;
     int32_t max_depth_seen;
+    int64_t excluded_centred;  /* dropped because some centred form F_c,i(X) excludes 0 */
 } orc_stats;
 
 typedef struct orc_result orc_result;
@@ -98,6 +101,8 @@ int orc_gj_inverse(int n, const double *a, double *inv);
 /* one Hansen-Sengupta sweep (Section 2.3, Algorithm 3):
  * returns 0 = box out (maybe unchanged), 1 = empty, 2 = skipped (singular) */
 int orc_hs_step(const orc_system *sys, const double *lo, const double *hi, double *out_lo, double *out_hi);
+/* centred form of every equation over the box (n_eqs == n_vars): out[i] = F_c,i(X) */
+void orc_centred(const orc_system *sys, const double *lo, const double *hi, double *out_lo, double *out_hi);
 
 #ifdef __cplusplus
 }

@@ -31,7 +31,7 @@ class ivs_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("hs_enable", C.c_int32), ("hs_min_depth", C.c_int32),
                 ("hs_iters", C.c_int32), ("prefilter_fp32", C.c_int32), ("root_depth", C.c_int32),
                 ("max_depth", C.c_int32), ("max_boxes", C.c_int64), ("max_results", C.c_int64),
-                ("time_budget_s", C.c_double)]
+                ("time_budget_s", C.c_double), ("centred_form", C.c_int32)]
 
 
 class ivs_stats(C.Structure):
@@ -40,7 +40,7 @@ class ivs_stats(C.Structure):
                 ("hs_singular", C.c_int64), ("accepted", C.c_int64), ("unsplittable", C.c_int64),
                 ("split", C.c_int64), ("max_depth_seen", C.c_int32), ("waves", C.c_int32),
                 ("device_ms", C.c_double), ("launches", C.c_int64), ("eval64_boxes", C.c_int64),
-                ("kept_shadow", C.c_int64), ("queue_ms", C.c_double), ("solve_ms", C.c_double)]
+                ("kept_shadow", C.c_int64), ("queue_ms", C.c_double), ("solve_ms", C.c_double), ("excluded_centred", C.c_int64)]
 
 
 class ivs_plan_cfg(C.Structure):
@@ -163,7 +163,8 @@ class _SysRef:
 
 
 def make_options(tol=1e-6, hs_enable=True, hs_min_depth=0, hs_iters=1, prefilter_fp32=True,
-                 root_depth=0, max_depth=200, max_boxes=0, max_results=0, time_budget_s=0.0):
+                 root_depth=0, max_depth=200, max_boxes=0, max_results=0, time_budget_s=0.0,
+                 centred_form=False):
     o = ivs_options()
     load().ivs_options_default(C.byref(o))
     o.tol = float(tol)
@@ -176,6 +177,7 @@ def make_options(tol=1e-6, hs_enable=True, hs_min_depth=0, hs_iters=1, prefilter
     o.max_boxes = int(max_boxes)
     o.max_results = int(max_results)
     o.time_budget_s = float(time_budget_s)
+    o.centred_form = int(bool(centred_form))
     return o
 
 

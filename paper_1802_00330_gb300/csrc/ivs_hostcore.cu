@@ -143,6 +143,8 @@ int validate(const ivs_system *s, const double *lo, const double *hi, const ivs_
         if (!std::isfinite(lo[j]) || !std::isfinite(hi[j]) || lo[j] > hi[j])
             return fail(IVS_ERR_INVALID, "bad initial box");
     if (o->hs_enable && s->n_eqs != s->n_vars) return fail(IVS_ERR_INVALID, "HS needs n_eqs == n_vars");
+    if (o->centred_form && s->n_eqs != s->n_vars)
+        return fail(IVS_ERR_INVALID, "the centred form needs n_eqs == n_vars");
     if (!(o->tol >= 0) || !std::isfinite(o->tol)) return fail(IVS_ERR_INVALID, "tol must be finite and >= 0");
     if (o->hs_iters < 0 || o->max_depth < 0 || o->max_depth > 0xFFF0 || o->root_depth < 0 ||
         o->root_depth > o->max_depth)
@@ -213,6 +215,7 @@ void compile_system(HostTables &h, const ivs_system *s, const ivs_options *o) {
     d.prefilter = o->prefilter_fp32 ? 1 : 0;
     d.shadow = 0;
     d.max_boxes = o->max_boxes;
+    d.centred = o->centred_form ? 1 : 0;
     pack_blob(h, bld, d, bld.poly_off[m]);
     h.sys.push_back(d);
 }

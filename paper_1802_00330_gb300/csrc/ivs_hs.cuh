@@ -83,7 +83,11 @@ struct Cfg {
     static constexpr int I_SLOT = N * BB;            // N: storage column of each original row
     static constexpr int I_SYS = 2 * N * BB;         // system of the box
     static constexpr int I_ITS = I_SYS + BB;         // HS sweeps the box gets
-    static constexpr int I_RUN = I_ITS + BB;         // box takes part in the current sweep
+    static constexpr int I_JF = I_ITS + BB;          // J(X) and f(x) needed in this pass
+    static constexpr int I_HS = I_JF + BB;           // HS sweep wanted in this pass
+    static constexpr int I_CEN = I_HS + BB;          // centred-form test in this pass
+    static constexpr int I_CEX = I_CEN + BB;         // the centred form excluded the box
+    static constexpr int I_RUN = I_CEX + BB;         // box takes part in the current sweep
     static constexpr int I_BAD = I_RUN + BB;         // singular preconditioner: sweep skipped
     static constexpr int I_EMPTY = I_BAD + BB;       // Gauss-Seidel left no point: box dropped
     static constexpr int INTS = I_EMPTY + BB;
@@ -105,25 +109,19 @@ struct ThinCol {
     }
 };
 
-// One Gauss-Seidel sweep on B f(x) + B J(X)(z - x) = 0 (eq 14, 21, 22) for every box of
-// the chunk with I_RUN set, by all threads of the block.  Leaves the result in Y and
-// sets I_EMPTY (no root) or I_BAD (singular preconditioner: the sweep is skipped).
+// J(X) from the derivative polynomials compiled on the host (units q < N^2), and f(x)
+// at the midpoint x = mid X as a thin-box evaluation (units N^2 + i), for every box of
+// the chunk with I_JF set, by all threads of the block.
 template <int N>
-__device__ __forceinline__ void hs_sweep_block(const SweepArgs &a, const char *blob_smem, double *sd, int *si,
-                                               int t) {
+__device__ __forceinline__ void jf_block(const SweepArgs &a, const char *blob_smem, double *sd, const int *si,
+                                         int t) {
     using C = Cfg<N>;
     constexpr int BB = C::BB, NT = C::NT;
-    double *J = sd + C::JM;   // interval (i, j): lo at (2 (i N + j)) BB, hi at (2 (i N + j) + 1) BB
-    double *G = sd + C::GB;   // point (i, j) at (i N + j) BB
-    const int *run = si + C::I_RUN;
-    int *bad = si + C::I_BAD;
-    int *empty = si + C::I_EMPTY;
-
-    // J(X) from the derivative polynomials compiled on the host (units q < N^2), and
-    // f(x) at the midpoint as a thin-box evaluation (units N^2 + i)
+    double *J = sd + C::JM;
+    const int *jf = si + C::I_JF;
     for (int e = t; e < (N * N + N) * BB; e += NT) {
         const int q = e / BB, b = e % BB;
-        if (!run[b]) continue;
+        if (!jf[b]) continue;
         const DevSys &S = a.tb.sys[si[C::I_SYS + b]];
         const SysTab Tb = make_tab(blob_smem ? blob_smem : a.tb.blobs + S.blob_off, S);
         if (q < N * N) {
@@ -138,6 +136,47 @@ __device__ __forceinline__ void hs_sweep_block(const SweepArgs &a, const char *b
         }
     }
     __syncthreads();
+}
+
+// Centred (mean-value) form from the expansion of Section 2.3 eq 13: for every y in X,
+// f_i(y) lies in F_c,i(X) = f_i(x) + sum_j J_ij(X) (X_j - x_j), folded left over
+// j = 1..n from f_i(x).  One equation per unit; sets I_CEX when some F_c,i excludes 0
+// (a NaN end never excludes).  Uses the J(X) and f(x) of jf_block.
+template <int N>
+__device__ __forceinline__ void centred_block(double *sd, int *si, int t) {
+    using C = Cfg<N>;
+    constexpr int BB = C::BB, NT = C::NT;
+    const double *J = sd + C::JM;
+    const int *cen = si + C::I_CEN;
+    for (int e = t; e < N * BB; e += NT) {
+        const int i = e / BB, b = e % BB;
+        if (!cen[b]) continue;
+        ivd acc = {sd[C::FR + (2 * i) * BB + b], sd[C::FR + (2 * i + 1) * BB + b]};
+#pragma unroll
+        for (int j = 0; j < N; j++) {
+            const double xc = sd[C::XC + j * BB + b];
+            const ivd d = iv_sub(ivd{sd[C::XLO + j * BB + b], sd[C::XHI + j * BB + b]}, ivd{xc, xc});
+            acc = iv_add(acc, iv_mul(ivd{J[(2 * (i * N + j)) * BB + b], J[(2 * (i * N + j) + 1) * BB + b]}, d));
+        }
+        if (d_pos(acc.lo) || d_neg(acc.hi)) atomicOr(&si[C::I_CEX + b], 1);
+    }
+    __syncthreads();
+}
+
+// One Gauss-Seidel sweep on B f(x) + B J(X)(z - x) = 0 (eq 14, 21, 22) for every box of
+// the chunk with I_RUN set (J(X) and f(x) already computed), by all threads of the block.
+// Leaves the result in Y and sets I_EMPTY (no root) or I_BAD (singular preconditioner:
+// the sweep is skipped).
+template <int N>
+__device__ __forceinline__ void hs_sweep_block(double *sd, int *si, int t) {
+    using C = Cfg<N>;
+    constexpr int BB = C::BB, NT = C::NT;
+    double *J = sd + C::JM;   // interval (i, j): lo at (2 (i N + j)) BB, hi at (2 (i N + j) + 1) BB
+    double *G = sd + C::GB;   // point (i, j) at (i N + j) BB
+    const int *run = si + C::I_RUN;
+    int *bad = si + C::I_BAD;
+    int *empty = si + C::I_EMPTY;
+
     // A = mid(J(X)), round to nearest
     for (int e = t; e < N * N * BB; e += NT) {
         const int q = e / BB, b = e % BB;
@@ -354,14 +393,13 @@ __global__ void __launch_bounds__(hsd::Cfg<N>::NT, hsd::Cfg<N>::MIN_BLOCKS) k_hs
         const long long base = s_base;
         if (base >= count) break;
         // the owners fetch their boxes: child `child` of queue entry `parent`
-        bool active = false, stopped = false, dropped = false;
-        int sys = 0, depth = 0;
+        bool active = false, stopped = false, dropped = false, dropped_c = false;
+        int sys = 0, depth = 0, its = 0, cen = 0;
         unsigned st_app = 0, st_con = 0, st_sing = 0;
         if (owner) {
             const int b = t;
             const long long idx = base + b;
             active = idx < count;
-            int its = 0;
             if (active) {
                 const Surv sv = list[idx];
                 const int64_t pi = sv.parent;
@@ -380,26 +418,46 @@ __global__ void __launch_bounds__(hsd::Cfg<N>::NT, hsd::Cfg<N>::MIN_BLOCKS) k_hs
                     sd[C::XC + j * BB + b] = midpoint_rn(lo, hi);
                 }
                 if (S.hs_enable && depth >= S.hs_min_depth) its = S.hs_iters > 0 ? S.hs_iters : 1;
+                cen = S.centred;
             }
             si[C::I_SYS + b] = sys;
-            si[C::I_ITS + b] = its;
+            si[C::I_ITS + b] = its > cen ? its : cen;   // passes: the centred test needs J, f once
         }
         __syncthreads();
         int max_it = 0;
         for (int b = 0; b < BB; b++) max_it = max(max_it, si[C::I_ITS + b]);
         for (int it = 0; it < max_it; it++) {
+            // pass `it`: J(X), f(x); on the first pass the centred test (if asked), then
+            // the Hansen-Sengupta sweep for the boxes that want one and were not excluded
             if (owner) {
                 const int b = t;
-                const bool run = active && !stopped && it < si[C::I_ITS + b];
-                si[C::I_RUN + b] = run ? 1 : 0;
+                const bool jf = active && !stopped && it < si[C::I_ITS + b];
+                si[C::I_JF + b] = jf ? 1 : 0;
+                si[C::I_HS + b] = (jf && it < its) ? 1 : 0;
+                si[C::I_CEN + b] = (jf && it == 0 && cen) ? 1 : 0;
+                si[C::I_CEX + b] = 0;
                 si[C::I_BAD + b] = 0;
                 si[C::I_EMPTY + b] = 0;
-                st_app += run ? 1u : 0u;
 #pragma unroll
                 for (int k = 0; k < N; k++) si[C::I_ROWID + k * BB + b] = k;
             }
             __syncthreads();
-            hs_sweep_block<N>(a, blob_smem, sd, si, t);
+            jf_block<N>(a, blob_smem, sd, si, t);
+            int any_cen = 0;
+            for (int b = 0; b < BB; b++) any_cen |= si[C::I_CEN + b];
+            if (any_cen) centred_block<N>(sd, si, t);
+            if (owner) {
+                const int b = t;
+                const bool run = si[C::I_HS + b] && !si[C::I_CEX + b];
+                si[C::I_RUN + b] = run ? 1 : 0;
+                st_app += run ? 1u : 0u;
+                if (si[C::I_CEX + b]) {
+                    dropped_c = true;
+                    stopped = true;
+                }
+            }
+            __syncthreads();
+            hs_sweep_block<N>(sd, si, t);
             if (owner && si[C::I_RUN + t]) {
                 const int b = t;
                 if (si[C::I_EMPTY + b]) {
@@ -428,10 +486,12 @@ __global__ void __launch_bounds__(hsd::Cfg<N>::NT, hsd::Cfg<N>::MIN_BLOCKS) k_hs
             const int b = t;
             int fate = 0;   // 0 none / dropped, 1 accepted, 2 new parent
             int flag = 0;
-            unsigned st_uns = 0, st_empty = 0;
+            unsigned st_uns = 0, st_empty = 0, st_cex = 0;
             if (active) {
                 const DevSys &S = a.tb.sys[sys];
-                if (dropped) {
+                if (dropped_c) {
+                    st_cex = 1;
+                } else if (dropped) {
                     st_empty = 1;
                 } else {
                     double w = 0.0;
@@ -521,19 +581,19 @@ __global__ void __launch_bounds__(hsd::Cfg<N>::NT, hsd::Cfg<N>::MIN_BLOCKS) k_hs
             }
             // statistics (new parents also enter the live count): one atomic per warp when
             // the warp holds a single system
-            unsigned v[8] = {st_app, st_empty, st_con, st_sing, (fate == 1 && flag != 4) ? 1u : 0u, st_uns,
-                             fate == 2 ? 1u : 0u, fate == 2 ? 1u : 0u};
-            const int slot[8] = {ST_HS_APPLIED, ST_HS_EMPTY, ST_HS_CONTRACTED, ST_HS_SINGULAR, ST_ACCEPTED,
-                                 ST_UNSPLITTABLE, ST_SPLIT, ST_LIVE};
+            unsigned v[9] = {st_app, st_empty, st_con, st_sing, (fate == 1 && flag != 4) ? 1u : 0u, st_uns,
+                             fate == 2 ? 1u : 0u, fate == 2 ? 1u : 0u, st_cex};
+            const int slot[9] = {ST_HS_APPLIED, ST_HS_EMPTY, ST_HS_CONTRACTED, ST_HS_SINGULAR, ST_ACCEPTED,
+                                 ST_UNSPLITTABLE, ST_SPLIT, ST_LIVE, ST_EXCL_CENTRED};
             if (uniform) {
 #pragma unroll
-                for (int q = 0; q < 8; q++) {
+                for (int q = 0; q < 9; q++) {
                     const unsigned tot = __reduce_add_sync(kFull, v[q]);
                     if (lane == 0 && tot) atomicAdd(stat_ptr(a, sys0, slot[q]), (unsigned long long)tot);
                 }
             } else if (active) {
 #pragma unroll
-                for (int q = 0; q < 8; q++)
+                for (int q = 0; q < 9; q++)
                     if (v[q]) atomicAdd(stat_ptr(a, sys, slot[q]), (unsigned long long)v[q]);
             }
         }

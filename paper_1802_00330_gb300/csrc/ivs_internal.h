@@ -32,6 +32,7 @@ enum Stat : int {
     ST_KEEP_SHADOW,    // boxes the FP32 shadow proved kept (no FP64 evaluation)
     ST_OUT,            // accepted boxes of the system (its result region holds min(this, out_cap))
     ST_LIVE,           // queue entries of the system (0 after a sweep: the system is solved)
+    ST_EXCL_CENTRED,   // boxes the centred form dropped
     ST_COUNT
 };
 constexpr int64_t kFlagResultOverflow = 1, kFlagDepthCut = 2, kFlagBudget = 4;
@@ -54,6 +55,7 @@ struct DevSys {
     int64_t out_cap;
     int32_t n_fterms;      // terms of the equations F_i
     int32_t n_tv;          // term-combination entries (0: no per-parent table)
+    int32_t centred;       // 1: centred-form exclusion test before Hansen-Sengupta
 };
 
 struct DevTables {

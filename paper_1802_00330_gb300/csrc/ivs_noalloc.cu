@@ -211,6 +211,8 @@ extern "C" int ivs_solve_noalloc(const ivs_system *s, const double *box_lo, cons
         if (!std::isfinite(box_lo[j]) || !std::isfinite(box_hi[j]) || box_lo[j] > box_hi[j])
             return err(IVS_ERR_INVALID, "ivs_solve_noalloc: bad initial box");
     if (o->hs_enable && m != n) return err(IVS_ERR_INVALID, "ivs_solve_noalloc: HS needs n_eqs == n_vars");
+    if (o->centred_form && m != n)
+        return err(IVS_ERR_INVALID, "ivs_solve_noalloc: the centred form needs n_eqs == n_vars");
     if (!(o->tol >= 0) || !std::isfinite(o->tol) || o->hs_iters < 0 || o->max_depth < 0 || o->max_depth > 0xFFF0 ||
         o->root_depth < 0 || o->root_depth > o->max_depth)
         return err(IVS_ERR_INVALID, "ivs_solve_noalloc: bad options");
@@ -230,6 +232,7 @@ extern "C" int ivs_solve_noalloc(const ivs_system *s, const double *box_lo, cons
     d.prefilter = o->prefilter_fp32 ? 1 : 0;
     d.shadow = 0;   // plain FP32 prefilter: sound whatever the magnitudes
     d.max_boxes = o->max_boxes;
+    d.centred = o->centred_form ? 1 : 0;
 
     // ---- set-up, once per device (with that device current) ----
     int dev = 0;
@@ -360,6 +363,7 @@ extern "C" int ivs_solve_noalloc(const ivs_system *s, const double *box_lo, cons
         stats->boxes = (int64_t)hs[ST_BOXES];
         stats->excluded_prefilter = (int64_t)hs[ST_EXCL_PREFILTER];
         stats->excluded_eval = (int64_t)hs[ST_EXCL_EVAL];
+        stats->excluded_centred = (int64_t)hs[ST_EXCL_CENTRED];
         stats->hs_applied = (int64_t)hs[ST_HS_APPLIED];
         stats->hs_empty = (int64_t)hs[ST_HS_EMPTY];
         stats->hs_contracted = (int64_t)hs[ST_HS_CONTRACTED];

@@ -36,7 +36,8 @@ def assert_same(g, o, check_stats=True):
         gs, os_ = g["stats"], o["stats"]
         assert gs["boxes"] == os_["boxes"]
         assert gs["excluded_prefilter"] + gs["excluded_eval"] == os_["excluded_eval"]
-        for k in ("hs_applied", "hs_empty", "hs_contracted", "hs_singular", "accepted", "unsplittable", "split"):
+        for k in ("hs_applied", "hs_empty", "hs_contracted", "hs_singular", "accepted", "unsplittable", "split",
+                  "excluded_centred"):
             assert gs[k] == os_[k], k
 
 
@@ -126,3 +127,35 @@ def test_budget_flags(gpu):
     s = synth.config_n6()
     g = gpu.solve(s, max_boxes=5000)
     assert g["status"] == 3
+
+
+@pytest.mark.parametrize("hs", [0, 1])
+def test_centred_form_bit_exact(gpu, orc, hs):
+    """The centred form as a second exclusion test (before Hansen-Sengupta): same boxes,
+    flags, depths and counters as the oracle, on small planted systems and on n=6."""
+    systems = synth.config_batched(count=10, seed=778, n_range=(2, 5))
+    removed = 0
+    for s in systems:
+        g = gpu.solve(s, hs_enable=hs, centred_form=True, tol=1e-4)
+        o = orc.solve(s, hs_enable=hs, centred=True, tol=1e-4)
+        assert_same(g, o)
+        removed += g["stats"]["excluded_centred"]
+    assert removed > 0
+    s = synth.config_n6()
+    assert_same(gpu.solve(s, centred_form=True), orc.solve(s, centred=True))
+
+
+def test_centred_form_with_iterated_sweeps_and_late_hs(gpu, orc):
+    """hs_iters = 2 and hs_min_depth = 3: the centred test runs at every depth before the
+    first sweep, the sweeps only from depth 3."""
+    systems = synth.config_batched(count=6, seed=779, n_range=(3, 5))
+    for s in systems:
+        kw = dict(hs_iters=2, hs_min_depth=3, tol=1e-4)
+        assert_same(gpu.solve(s, centred_form=True, **kw), orc.solve(s, centred=True, **kw))
+
+
+def test_centred_form_in_a_batch(gpu, orc):
+    systems = synth.config_batched(count=16, seed=780, n_range=(2, 5))
+    outs = gpu.solve_batch(systems, centred_form=True, tol=1e-4)
+    for s, g in zip(systems, outs):
+        assert_same(g, orc.solve(s, centred=True, tol=1e-4))
