@@ -121,7 +121,12 @@ void ivs_options_default(ivs_options *o);
 
 /* Solve one system on the initial box [box_lo, box_hi] (n_vars doubles each).
  * On IVS_OK / IVS_ERR_BUDGET / IVS_ERR_TIMEOUT *out receives a result (free it with
- * ivs_result_free); on other errors *out is NULL. */
+ * ivs_result_free); on other errors *out is NULL.
+ * ivs_solve and ivs_solve_batch keep the device memory, stream, pinned buffers and
+ * instantiated CUDA graph of their last call (device 0) and build the next call from
+ * them; calls from several threads are safe (each takes the kept set or makes its own).
+ * ivs_release_cached frees what is kept. */
+void ivs_release_cached(void);
 int ivs_solve(const ivs_system *sys, const double *box_lo, const double *box_hi,
               const ivs_options *opt, ivs_result **out);
 

@@ -70,6 +70,7 @@ _VP = C.c_void_p
 _PP = C.POINTER(C.c_void_p)
 SIGNATURES = {
     "ivs_options_default": (None, [C.POINTER(ivs_options)]),
+    "ivs_release_cached": (None, []),
     "ivs_solve": (C.c_int, [C.POINTER(ivs_system), _VP, _VP, C.POINTER(ivs_options), _PP]),
     "ivs_solve_batch": (C.c_int, [C.c_int32, C.POINTER(ivs_system), _VP, _VP, C.POINTER(ivs_options),
                                   C.c_int32, _PP]),
@@ -377,9 +378,26 @@ def autotune(systems, trial_boxes=200_000, **opts):
 
 
 def solve_batch(systems, **opts):
-    plan = Plan(systems, opts=opts or None)
+    """Solve many systems in one device run through ``ivs_solve_batch``."""
+    lib = load()
+    refs = [_SysRef(s) for s in systems]
+    n = len(systems)
+    arr = (ivs_system * n)(*[r.c for r in refs])
+    los = (C.c_void_p * n)(*[_ptr(r.lo) for r in refs])
+    his = (C.c_void_p * n)(*[_ptr(r.hi) for r in refs])
+    oarr = (ivs_options * n)(*[make_options(**{"tol": s.tol, **opts}) for s in systems])
+    outs = (C.c_void_p * n)()
+    rc = lib.ivs_solve_batch(n, arr, los, his, oarr, C.sizeof(ivs_options), outs)
     try:
-        plan.run()
-        return [plan.result(s) for s in range(len(systems))]
+        if any(not o for o in outs):
+            _check(rc)
+        return [result_to_dict(o) for o in outs]
     finally:
-        plan.close()
+        for o in outs:
+            if o:
+                lib.ivs_result_free(o)
+
+
+def release_cached():
+    """Frees the device memory, stream and graph that ivs_solve keeps from its last call."""
+    load().ivs_release_cached()

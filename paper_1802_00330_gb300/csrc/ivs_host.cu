@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -51,7 +52,9 @@ struct ivs_plan {
     bool own_stream = false;
     void *ws = nullptr;
     bool own_ws = false;
+    size_t ws_bytes = 0;
     void *tables_mem = nullptr;
+    size_t tables_bytes = 0;
     SweepArgs args{};
     int64_t wave_children = 0, queue_cap = 0, out_cap = 0;
     double *d_box_lo = nullptr, *d_box_hi = nullptr;
@@ -129,9 +132,31 @@ void ivs_plan_destroy(ivs_plan *p) {
     delete p;
 }
 
-int ivs_plan_create(int32_t n_sys, const ivs_system *systems, const double *const *box_lo,
-                    const double *const *box_hi, const ivs_options *opts, int32_t opts_stride,
-                    const ivs_plan_cfg *cfg, ivs_plan **out) {
+}  // extern "C"
+
+namespace {
+
+bool same_args(const SweepArgs &x, const SweepArgs &y) {
+    auto same_q = [](const DevQueue &a, const DevQueue &b) {
+        return a.lo == b.lo && a.mid == b.mid && a.hi == b.hi && a.sys == b.sys && a.meta == b.meta && a.cap == b.cap;
+    };
+    return x.tb.sys == y.tb.sys && x.tb.blobs == y.tb.blobs && same_q(x.q, y.q) && same_q(x.stage, y.stage) &&
+           x.out.lo == y.out.lo && x.out.hi == y.out.hi && x.out.sys == y.out.sys && x.out.flags == y.out.flags &&
+           x.out.depth == y.out.depth && x.out.cap == y.out.cap && x.ctl == y.ctl && x.surv == y.surv &&
+           x.surv_cap == y.surv_cap && x.cand == y.cand && x.stats == y.stats &&
+           x.wave_children == y.wave_children && x.max_fan_shift == y.max_fan_shift && x.n_sys == y.n_sys &&
+           x.single == y.single && x.blob_smem == y.blob_smem && x.tv_stride == y.tv_stride &&
+           x.eval_warps == y.eval_warps;
+}
+
+// Builds a plan.  With `reuse` (a plan that is no longer needed) its stream, events,
+// pinned buffers, device memory (when large enough) and instantiated graph (when the
+// kernels' arguments come out the same) move into the new plan instead of being
+// created again; the rest of `reuse` is freed.
+int plan_create_impl(int32_t n_sys, const ivs_system *systems, const double *const *box_lo,
+                     const double *const *box_hi, const ivs_options *opts, int32_t opts_stride,
+                     const ivs_plan_cfg *cfg, ivs_plan *reuse, ivs_plan **out) {
+    std::unique_ptr<ivs_plan, void (*)(ivs_plan *)> old(reuse, ivs_plan_destroy);
     if (!out) return fail(IVS_ERR_INVALID, "null out");
     *out = nullptr;
     if (n_sys <= 0 || !systems || !box_lo || !box_hi || !opts) return fail(IVS_ERR_INVALID, "bad arguments");
@@ -183,15 +208,27 @@ int ivs_plan_create(int32_t n_sys, const ivs_system *systems, const double *cons
     p->device = c.device;
     CUDA_TRY(cudaSetDevice(p->device));
     CUDA_TRY(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+    ivs_plan *r = (old && old->device == p->device) ? old.get() : nullptr;
+    if (r && r->stream) CUDA_TRY(cudaStreamSynchronize(r->stream));
     if (c.stream) {
         p->stream = (cudaStream_t)c.stream;
+    } else if (r && r->own_stream) {
+        std::swap(p->stream, r->stream);
+        r->own_stream = false;
+        p->own_stream = true;
     } else {
         CUDA_TRY(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
         p->own_stream = true;
     }
-    CUDA_TRY(cudaEventCreate(&p->ev0));
-    CUDA_TRY(cudaEventCreate(&p->ev1));
-    CUDA_TRY(cudaMallocHost((void **)&p->h_ctl, sizeof(WaveCtl)));
+    if (r && r->ev0 && r->ev1) {
+        std::swap(p->ev0, r->ev0);
+        std::swap(p->ev1, r->ev1);
+    } else {
+        CUDA_TRY(cudaEventCreate(&p->ev0));
+        CUDA_TRY(cudaEventCreate(&p->ev1));
+    }
+    if (r && r->h_ctl) std::swap(p->h_ctl, r->h_ctl);
+    else CUDA_TRY(cudaMallocHost((void **)&p->h_ctl, sizeof(WaveCtl)));
 
     // workspace: wave size W, queue capacity Q, result capacity O
     const int64_t W = c.wave_children > 0 ? c.wave_children : (int64_t)1 << 22;
@@ -207,8 +244,20 @@ int ivs_plan_create(int32_t n_sys, const ivs_system *systems, const double *cons
         Q = (int64_t)((want - fixed - 64 * 1024) / per_parent);
         if (Q < 16) return fail(IVS_ERR_NOMEM, "workspace too small");
         size_t total = layout_for(n_sys, p->n_max, W, Q, out_cap).total;
-        cudaError_t e = cudaMalloc(&p->ws, total);
-        if (e != cudaSuccess) return fail(IVS_ERR_NOMEM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
+        if (r && r->own_ws && r->ws_bytes >= total) {
+            std::swap(p->ws, r->ws);
+            p->ws_bytes = r->ws_bytes;
+            r->own_ws = false;
+        } else {
+            if (r && r->own_ws && r->ws) {   // too small: give it back before allocating
+                cudaFree(r->ws);
+                r->ws = nullptr;
+                r->own_ws = false;
+            }
+            cudaError_t e = cudaMalloc(&p->ws, total);
+            if (e != cudaSuccess) return fail(IVS_ERR_NOMEM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
+            p->ws_bytes = total;
+        }
         p->own_ws = true;
     }
     if (Q < n_sys) return fail(IVS_ERR_NOMEM, "queue cannot hold the initial boxes");
@@ -239,7 +288,14 @@ int ivs_plan_create(int32_t n_sys, const ivs_system *systems, const double *cons
 
     // tables: the DevSys array and the blob arena in one allocation
     const size_t sys_bytes = align_up(h.sys.size() * sizeof(DevSys), 256);
-    CUDA_TRY(cudaMalloc(&p->tables_mem, sys_bytes + std::max<size_t>(h.blobs.size(), 16)));
+    const size_t tables_need = sys_bytes + std::max<size_t>(h.blobs.size(), 16);
+    if (r && r->tables_mem && r->tables_bytes >= tables_need) {
+        std::swap(p->tables_mem, r->tables_mem);
+        p->tables_bytes = r->tables_bytes;
+    } else {
+        CUDA_TRY(cudaMalloc(&p->tables_mem, tables_need));
+        p->tables_bytes = tables_need;
+    }
     CUDA_TRY(cudaMemcpyAsync(p->tables_mem, h.sys.data(), h.sys.size() * sizeof(DevSys), cudaMemcpyHostToDevice,
                              p->stream));
     if (!h.blobs.empty())
@@ -272,15 +328,62 @@ int ivs_plan_create(int32_t n_sys, const ivs_system *systems, const double *cons
     // profiling needs per-stage events, which a graph body cannot hold: host loop then
     p->use_graph = !p->profile && std::getenv("IVS_HOST_LOOP") == nullptr;
     if (p->use_graph) {
-        CUDA_TRY(cudaMallocHost((void **)&p->h_wave_limit, sizeof(int64_t)));
-        CUDA_TRY(build_sweep_graph(a, p->dims.data(), (int)p->dims.size(), p->eval_blocks, p->eval_threads,
-                                   p->num_sms, &p->graph));
-        CUDA_TRY(cudaGraphInstantiate(&p->graph_exec, p->graph, 0));
+        if (r && r->h_wave_limit) std::swap(p->h_wave_limit, r->h_wave_limit);
+        else CUDA_TRY(cudaMallocHost((void **)&p->h_wave_limit, sizeof(int64_t)));
+        if (r && r->graph_exec && same_args(r->args, a) && r->dims == p->dims && r->eval_blocks == p->eval_blocks &&
+            r->eval_threads == p->eval_threads && r->num_sms == p->num_sms) {
+            std::swap(p->graph, r->graph);          // same kernels, same arguments: same graph
+            std::swap(p->graph_exec, r->graph_exec);
+        } else {
+            CUDA_TRY(build_sweep_graph(a, p->dims.data(), (int)p->dims.size(), p->eval_blocks, p->eval_threads,
+                                       p->num_sms, &p->graph));
+            CUDA_TRY(cudaGraphInstantiate(&p->graph_exec, p->graph, 0));
+        }
     }
     p->class_ms.assign(3 + p->dims.size(), 0.0);
     p->class_launches.assign(3 + p->dims.size(), 0);
     *out = p.release();
     return IVS_OK;
+}
+
+// ivs_solve / ivs_solve_batch keep the plan of their last call per device and build
+// the next one from its resources
+std::mutex g_cache_mu;
+constexpr int kCacheDevices = 64;
+ivs_plan *g_cache[kCacheDevices] = {};
+
+ivs_plan *cache_take(int device) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    if (device < 0 || device >= kCacheDevices) return nullptr;
+    ivs_plan *p = g_cache[device];
+    g_cache[device] = nullptr;
+    return p;
+}
+
+void cache_put(ivs_plan *p) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        if (p->device >= 0 && p->device < kCacheDevices && !g_cache[p->device]) {
+            g_cache[p->device] = p;
+            return;
+        }
+    }
+    ivs_plan_destroy(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ivs_plan_create(int32_t n_sys, const ivs_system *systems, const double *const *box_lo,
+                    const double *const *box_hi, const ivs_options *opts, int32_t opts_stride,
+                    const ivs_plan_cfg *cfg, ivs_plan **out) {
+    return plan_create_impl(n_sys, systems, box_lo, box_hi, opts, opts_stride, cfg, nullptr, out);
+}
+
+void ivs_release_cached(void) {
+    for (int d = 0; d < kCacheDevices; d++) ivs_plan_destroy(cache_take(d));
 }
 
 int ivs_plan_run(ivs_plan *p) {
@@ -521,7 +624,7 @@ int ivs_solve_batch(int32_t n_sys, const ivs_system *systems, const double *cons
     if (!outs) return fail(IVS_ERR_INVALID, "null outs");
     for (int s = 0; s < n_sys; s++) outs[s] = nullptr;
     ivs_plan *p = nullptr;
-    int rc = ivs_plan_create(n_sys, systems, box_lo, box_hi, opts, opts_stride, nullptr, &p);
+    int rc = plan_create_impl(n_sys, systems, box_lo, box_hi, opts, opts_stride, nullptr, cache_take(0), &p);
     if (rc) return rc;
     int run = ivs_plan_run(p);
     if (run != IVS_OK && run != IVS_ERR_TIMEOUT && run != IVS_ERR_NOMEM) {
@@ -537,7 +640,7 @@ int ivs_solve_batch(int32_t n_sys, const ivs_system *systems, const double *cons
         }
         if (first == IVS_OK && outs[s]->status != IVS_OK) first = outs[s]->status;
     }
-    ivs_plan_destroy(p);
+    cache_put(p);
     return first;
 }
 

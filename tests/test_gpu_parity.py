@@ -159,3 +159,19 @@ def test_centred_form_in_a_batch(gpu, orc):
     outs = gpu.solve_batch(systems, centred_form=True, tol=1e-4)
     for s, g in zip(systems, outs):
         assert_same(g, orc.solve(s, centred=True, tol=1e-4))
+
+
+def test_repeated_solves_reuse_and_stay_exact(gpu, orc):
+    """ivs_solve builds each call from the previous call's device memory, stream and
+    (when the kernels' arguments match) graph: alternating systems of different shapes,
+    repeated calls and a release in between all give the oracle's results."""
+    a = synth.config_n2()
+    b = synth.config_batched(count=3, seed=901, n_range=(3, 4))
+    expect = {id(s): orc.solve(s) for s in [a] + b}
+    for s in [a, a, b[0], b[0], a, b[1], b[2], b[2]]:
+        assert_same(gpu.solve(s), expect[id(s)])
+    gpu.release_cached()
+    assert_same(gpu.solve(a), expect[id(a)])
+    outs = gpu.solve_batch(b)
+    for s, g in zip(b, outs):
+        assert_same(g, expect[id(s)])
