@@ -376,6 +376,19 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
                 "work": work, "kernel_share": dom[1][1] / sum(v[1] for v in ktimes.values()),
                 "avg_launch_ms": dom[1][1] / max(1, dom[1][0])}
 
+    # the FP32 stage (evaluation kernel): natural-form operations of every child it
+    # evaluates, against the measured directed FP32 rate
+    ev_ms = ktimes.get("eval", (0, 0.0))[1]
+    ev_ops = pst["boxes"] * np.mean([eval_ops(s) for s in systems]) * n_steps
+    prefilter_roofline = None
+    if ev_ms > 0:
+        ach32 = ev_ops / (ev_ms * 1e-3) / 1e12
+        prefilter_roofline = {"bound": "alu", "kernel": "eval", "achieved": ach32, "peak": fp32_rate / 1e12,
+                              "unit": "TFLOP/s", "frac": ach32 / (fp32_rate / 1e12),
+                              "work": "FP32 natural-form ops per child (the FP64 count of one evaluation) x "
+                                      "children through the FP32 stage",
+                              "peak_source": "measured in this run: directed __fadd_rd/__fmul_ru probe"}
+
     out = None
     if rank == 0:
         cpu = None
@@ -395,7 +408,7 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
                                 "ms_per_step": 1e3 * float(np.mean(t64))},
             "e2e": e2e,
             "gpu_launches": int(launches),
-            "roofline": roofline,
+            "roofline": roofline, "prefilter_roofline": prefilter_roofline,
             "measured_rates": {"fp64_directed_ops_per_s": fp64_rate, "fp32_directed_ops_per_s": fp32_rate},
             "kernel_ms": {k: round(v[1], 4) for k, v in ktimes.items()},
             "host_loop_ms_per_step": 1e3 * float(np.mean(prof_t)),

@@ -22,6 +22,7 @@
 // Templated on n; the instantiations are spread over several translation units
 // (ivs_hs_*.cu).
 #pragma once
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "ivs_internal.h"
@@ -31,8 +32,12 @@
 
 namespace ivs {
 
+namespace cg = cooperative_groups;
+
 namespace hsd {
 constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kCS = 4;          // CTAs per cluster in the cooperative form
+constexpr int kCoopMaxN = 12;   // the cooperative form exists for n <= 12
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
 __device__ __forceinline__ unsigned long long *stat_ptr(const SweepArgs &a, int sys, int slot) {
@@ -112,30 +117,61 @@ struct ThinCol {
 // J(X) from the derivative polynomials compiled on the host (units q < N^2), and f(x)
 // at the midpoint x = mid X as a thin-box evaluation (units N^2 + i), for every box of
 // the chunk with I_JF set, by all threads of the block.
-template <int N>
+// In the cooperative form (COOP) the cluster's CTAs share the units and every result is
+// written into each CTA's copy of the chunk (distributed shared memory); the barrier in
+// front keeps a fast CTA from overwriting J or f while a peer still reads the last pass's.
+template <int N, bool COOP>
 __device__ __forceinline__ void jf_block(const SweepArgs &a, const char *blob_smem, double *sd, const int *si,
                                          int t) {
     using C = Cfg<N>;
     constexpr int BB = C::BB, NT = C::NT;
-    double *J = sd + C::JM;
     const int *jf = si + C::I_JF;
-    for (int e = t; e < (N * N + N) * BB; e += NT) {
+    int gt = t, GT = NT;
+    if (COOP) {
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        gt = (int)cl.block_rank() * NT + t;
+        GT = kCS * NT;
+    }
+    for (int e = gt; e < (N * N + N) * BB; e += GT) {
         const int q = e / BB, b = e % BB;
         if (!jf[b]) continue;
         const DevSys &S = a.tb.sys[si[C::I_SYS + b]];
         const SysTab Tb = make_tab(blob_smem ? blob_smem : a.tb.blobs + S.blob_off, S);
+        ivd v;
+        double *dst;
         if (q < N * N) {
-            const ivd v = poly64(Tb, S.j_poly + q, BoxCol<BB>{sd + C::XLO + b, sd + C::XHI + b});
-            J[(2 * q) * BB + b] = v.lo;
-            J[(2 * q + 1) * BB + b] = v.hi;
+            v = poly64(Tb, S.j_poly + q, BoxCol<BB>{sd + C::XLO + b, sd + C::XHI + b});
+            dst = sd + C::JM + (2 * q) * BB + b;
         } else {
             const int i = q - N * N;
-            const ivd v = poly64(Tb, S.f_poly + i, ThinCol<BB>{sd + C::XC + b});
-            sd[C::FR + (2 * i) * BB + b] = v.lo;
-            sd[C::FR + (2 * i + 1) * BB + b] = v.hi;
+            v = poly64(Tb, S.f_poly + i, ThinCol<BB>{sd + C::XC + b});
+            dst = sd + C::FR + (2 * i) * BB + b;
+        }
+        if (COOP) {
+            cg::cluster_group cl = cg::this_cluster();
+#pragma unroll
+            for (int r = 0; r < kCS; r++) {
+                double *d = cl.map_shared_rank(dst, r);
+                d[0] = v.lo;
+                d[BB] = v.hi;
+            }
+        } else {
+            dst[0] = v.lo;
+            dst[BB] = v.hi;
         }
     }
-    __syncthreads();
+    if (COOP) cg::this_cluster().sync();
+    else __syncthreads();
+}
+
+// rows per unit of the cooperative M = B J(X): the fewest that give every unit its own
+// warp of the cluster
+template <int N>
+__host__ __device__ constexpr int coop_rows() {
+    int r = 1;
+    while ((N + 1) * ((N + r - 1) / r) > kCS * Cfg<N>::NW) r++;
+    return r;
 }
 
 // Centred (mean-value) form from the expansion of Section 2.3 eq 13: for every y in X,
@@ -167,15 +203,16 @@ __device__ __forceinline__ void centred_block(double *sd, int *si, int t) {
 // the chunk with I_RUN set (J(X) and f(x) already computed), by all threads of the block.
 // Leaves the result in Y and sets I_EMPTY (no root) or I_BAD (singular preconditioner:
 // the sweep is skipped).
+// Parts: gj_block (mid J(X), Gauss-Jordan, column order), m_block (M = B J(X), r = B f(x)),
+// gs_block (Gauss-Seidel); each ends with a barrier.
 template <int N>
-__device__ __forceinline__ void hs_sweep_block(double *sd, int *si, int t) {
+__device__ __forceinline__ void gj_block(double *sd, int *si, int t) {
     using C = Cfg<N>;
     constexpr int BB = C::BB, NT = C::NT;
     double *J = sd + C::JM;   // interval (i, j): lo at (2 (i N + j)) BB, hi at (2 (i N + j) + 1) BB
     double *G = sd + C::GB;   // point (i, j) at (i N + j) BB
     const int *run = si + C::I_RUN;
     int *bad = si + C::I_BAD;
-    int *empty = si + C::I_EMPTY;
 
     // A = mid(J(X)), round to nearest
     for (int e = t; e < N * N * BB; e += NT) {
@@ -268,9 +305,53 @@ __device__ __forceinline__ void hs_sweep_block(double *sd, int *si, int t) {
         if (nf) atomicOr(&bad[b], 1);
     }
     __syncthreads();
-    // M = B J(X) in place of J, one column per unit; r = B f(x) in place of f (unit N)
-    // (Algorithm 4, outward, u = 1..n in order; starting from the first product equals
-    // starting from [0,0])
+}
+
+// M = B J(X) in place of J, one column per unit; r = B f(x) in place of f (unit N)
+// (Algorithm 4, outward, u = 1..n in order; starting from the first product equals
+// starting from [0,0]).  Cooperative form: units are (column, block of coop_rows rows)
+// spread over the cluster, each holds its column in registers across a barrier before
+// any entry is overwritten, and writes its entries into every CTA's copy.
+template <int N, bool COOP>
+__device__ __forceinline__ void m_block(double *sd, const int *si, int t) {
+    using C = Cfg<N>;
+    constexpr int BB = C::BB, NT = C::NT;
+    double *J = sd + C::JM;
+    const double *G = sd + C::GB;
+    const int *run = si + C::I_RUN;
+    const int *bad = si + C::I_BAD;
+    if constexpr (COOP) {
+        constexpr int RB = coop_rows<N>(), NH = (N + RB - 1) / RB, U = (N + 1) * NH;
+        cg::cluster_group cl = cg::this_cluster();
+        const int gt = (int)cl.block_rank() * NT + t;
+        const int u = gt / BB, b = gt % BB;
+        const bool on = u < U && run[b] && !bad[b];
+        const int j = u / NH, h = u % NH;
+        ivd col[N];
+        if (on) {
+#pragma unroll
+            for (int v = 0; v < N; v++)
+                col[v] = (j < N) ? ivd{J[(2 * (v * N + j)) * BB + b], J[(2 * (v * N + j) + 1) * BB + b]}
+                                 : ivd{sd[C::FR + (2 * v) * BB + b], sd[C::FR + (2 * v + 1) * BB + b]};
+        }
+        cl.sync();   // every column is read before any entry is overwritten
+        if (on) {
+            const int i1 = min(N, (h + 1) * RB);
+            for (int i = h * RB; i < i1; i++) {
+                ivd acc = iv_smul(G[(i * N) * BB + b], col[0]);
+#pragma unroll
+                for (int v = 1; v < N; v++) acc = iv_add(acc, iv_smul(G[(i * N + v) * BB + b], col[v]));
+                double *dst = (j < N) ? J + (2 * (i * N + j)) * BB + b : sd + C::FR + (2 * i) * BB + b;
+#pragma unroll
+                for (int r = 0; r < kCS; r++) {
+                    double *d = cl.map_shared_rank(dst, r);
+                    d[0] = acc.lo;
+                    d[BB] = acc.hi;
+                }
+            }
+        }
+        cl.sync();
+    } else {
     for (int e = t; e < (N + 1) * BB; e += NT) {
         const int j = e / BB, b = e % BB;
         if (!run[b] || bad[b]) continue;
@@ -292,10 +373,21 @@ __device__ __forceinline__ void hs_sweep_block(double *sd, int *si, int t) {
         }
     }
     __syncthreads();
-    // Gauss-Seidel (eq 21-22).  Row i folds r_i and the products M_ij (Y_j - x_j), j != i,
-    // in order j = 1..n; products with j > i use the box's own coordinates and are formed
-    // up front, those with j < i as soon as Y_j is final.  A product is written over M_ij,
-    // which nothing reads afterwards.
+    }
+}
+
+// Gauss-Seidel (eq 21-22).  Row i folds r_i and the products M_ij (Y_j - x_j), j != i,
+// in order j = 1..n; products with j > i use the box's own coordinates and are formed
+// up front, those with j < i as soon as Y_j is final.  A product is written over M_ij,
+// which nothing reads afterwards.
+template <int N>
+__device__ __forceinline__ void gs_block(double *sd, int *si, int t) {
+    using C = Cfg<N>;
+    constexpr int BB = C::BB, NT = C::NT;
+    double *J = sd + C::JM;
+    const int *run = si + C::I_RUN;
+    const int *bad = si + C::I_BAD;
+    int *empty = si + C::I_EMPTY;
     for (int e = t; e < N * BB; e += NT) {
         const int i = e / BB, b = e % BB;
         sd[C::YLO + i * BB + b] = sd[C::XLO + i * BB + b];
@@ -365,13 +457,22 @@ __device__ __forceinline__ void hs_sweep_block(double *sd, int *si, int t) {
 }
 }  // namespace hsd
 
-template <int N>
-__global__ void __launch_bounds__(hsd::Cfg<N>::NT, hsd::Cfg<N>::MIN_BLOCKS) k_hs(SweepArgs a, int cache_blob) {
+// The kernel body.  Independent form (COOP = false): every CTA takes its own chunks.
+// Cooperative form (COOP = true, clusters of kCS CTAs, one CTA per SM): a cluster takes
+// a chunk and its CTAs work on it together -- each keeps a full copy of the chunk's state
+// and runs the serial parts itself (identical results on every copy), while J(X), f(x)
+// and M = B J(X) are shared out over the cluster's warps.  A sweep with at most coop_max
+// boxes runs in the cooperative form, larger ones in the independent form (the other
+// kernel returns at once).
+template <int N, bool COOP>
+__device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int64_t coop_max) {
     using namespace hsd;
     using C = Cfg<N>;
     constexpr int BB = C::BB;
     extern __shared__ __align__(16) char smem[];
-    __shared__ long long s_base;
+    // chunk index, two slots used in turn: in the cooperative form the cluster's first CTA
+    // writes the next chunk's slot while a peer may not yet have read the current one
+    __shared__ long long s_base[2];
     const int t = threadIdx.x, lane = (int)lane_id();
     const size_t blob_bytes = cache_blob ? (size_t)a.blob_smem : 0;
     double *sd = reinterpret_cast<double *>(smem + blob_bytes);
@@ -379,7 +480,13 @@ __global__ void __launch_bounds__(hsd::Cfg<N>::NT, hsd::Cfg<N>::MIN_BLOCKS) k_hs
 
     WaveCtl *ctl = a.ctl;
     const int64_t count = ctl->surv_count[N];
-    if ((int64_t)blockIdx.x * BB >= count) return;   // not needed for this many boxes
+    if (COOP ? count > coop_max : count <= coop_max) return;   // the other form's sweep
+    int rank = 0, group = blockIdx.x;                         // group: this CTA or cluster
+    if (COOP) {
+        rank = (int)cg::this_cluster().block_rank();
+        group = blockIdx.x / kCS;
+    }
+    if ((int64_t)group * BB >= count) return;   // not needed for this many boxes (whole clusters)
     if (cache_blob) {
         const DevSys &S0 = a.tb.sys[0];
         copy_blob(smem, a.tb.blobs + S0.blob_off, (uint32_t)S0.blob_bytes);   // visible after the next barrier
@@ -387,10 +494,20 @@ __global__ void __launch_bounds__(hsd::Cfg<N>::NT, hsd::Cfg<N>::MIN_BLOCKS) k_hs
     const char *blob_smem = cache_blob ? smem : nullptr;
     const Surv *list = a.surv + (size_t)N * a.surv_cap;
     const bool owner = t < BB;   // owner thread of box b = t
-    for (;;) {
-        if (t == 0) s_base = (long long)atomicAdd((unsigned long long *)&ctl->hs_cursor[N], (unsigned long long)BB);
-        __syncthreads();
-        const long long base = s_base;
+    for (int slot = 0;; slot ^= 1) {
+        if (COOP) {
+            cg::cluster_group cl = cg::this_cluster();
+            if (rank == 0 && t == 0) {
+                const long long v = (long long)atomicAdd((unsigned long long *)&ctl->hs_cursor[N], (unsigned long long)BB);
+#pragma unroll
+                for (int r = 0; r < kCS; r++) *cl.map_shared_rank(&s_base[slot], r) = v;
+            }
+            cl.sync();
+        } else {
+            if (t == 0) s_base[slot] = (long long)atomicAdd((unsigned long long *)&ctl->hs_cursor[N], (unsigned long long)BB);
+            __syncthreads();
+        }
+        const long long base = s_base[slot];
         if (base >= count) break;
         // the owners fetch their boxes: child `child` of queue entry `parent`
         bool active = false, stopped = false, dropped = false, dropped_c = false;
@@ -442,7 +559,7 @@ __global__ void __launch_bounds__(hsd::Cfg<N>::NT, hsd::Cfg<N>::MIN_BLOCKS) k_hs
                 for (int k = 0; k < N; k++) si[C::I_ROWID + k * BB + b] = k;
             }
             __syncthreads();
-            jf_block<N>(a, blob_smem, sd, si, t);
+            jf_block<N, COOP>(a, blob_smem, sd, si, t);
             int any_cen = 0;
             for (int b = 0; b < BB; b++) any_cen |= si[C::I_CEN + b];
             if (any_cen) centred_block<N>(sd, si, t);
@@ -457,7 +574,9 @@ __global__ void __launch_bounds__(hsd::Cfg<N>::NT, hsd::Cfg<N>::MIN_BLOCKS) k_hs
                 }
             }
             __syncthreads();
-            hs_sweep_block<N>(sd, si, t);
+            gj_block<N>(sd, si, t);
+            m_block<N, COOP>(sd, si, t);
+            gs_block<N>(sd, si, t);
             if (owner && si[C::I_RUN + t]) {
                 const int b = t;
                 if (si[C::I_EMPTY + b]) {
@@ -481,8 +600,9 @@ __global__ void __launch_bounds__(hsd::Cfg<N>::NT, hsd::Cfg<N>::MIN_BLOCKS) k_hs
             }
             __syncthreads();
         }
-        // Algorithm 1 termination (II) and the split, by warp 0 (lane b owns box b)
-        if (t < 32) {
+        // Algorithm 1 termination (II) and the split, by warp 0 (lane b owns box b); in the
+        // cooperative form only the cluster's first CTA writes
+        if (t < 32 && rank == 0) {
             const int b = t;
             int fate = 0;   // 0 none / dropped, 1 accepted, 2 new parent
             int flag = 0;
@@ -599,21 +719,64 @@ __global__ void __launch_bounds__(hsd::Cfg<N>::NT, hsd::Cfg<N>::MIN_BLOCKS) k_hs
         }
         __syncthreads();   // the chunk's arrays and s_base are reused by the next chunk
     }
+    if (COOP) cg::this_cluster().sync();   // no CTA leaves while a peer may still write to it
+}
+
+template <int N>
+__global__ void __launch_bounds__(hsd::Cfg<N>::NT, hsd::Cfg<N>::MIN_BLOCKS)
+    k_hs(SweepArgs a, int cache_blob, long long coop_max) {
+    hs_body<N, false>(a, cache_blob, coop_max);
+}
+
+template <int N>
+__global__ void __cluster_dims__(hsd::kCS, 1, 1) __launch_bounds__(hsd::Cfg<N>::NT, 1)
+    k_hs_coop(SweepArgs a, int cache_blob, long long coop_max) {
+    hs_body<N, true>(a, cache_blob, coop_max);
 }
 
 // ---- launcher -------------------------------------------------------------------
 
 // largest dynamic shared memory a block may use (227 KB less the static s_base)
 constexpr size_t kHsSmemLimit = 227 * 1024 - 64;
+// a cooperative CTA asks for at least this much, so no two share an SM
+constexpr size_t kOneCtaPerSm = 120 * 1024;
 
 template <int N>
 static cudaError_t launch_hs_n(const SweepArgs &a, int num_sms, cudaStream_t st) {
     using C = hsd::Cfg<N>;
     static int per_sm = 0;             // blocks per SM, found once per configuration
-    static size_t configured_smem = 0;
+    static size_t configured_smem = 0, configured_coop = 0;
     // cache the term table in shared memory when the plan holds one system and it fits
     const bool cache = a.single && (size_t)a.blob_smem + C::BYTES <= kHsSmemLimit;
     const size_t smem = (cache ? (size_t)a.blob_smem : 0) + C::BYTES;
+    long long coop_max = 0;
+    if constexpr (N <= hsd::kCoopMaxN) {
+      if (num_sms >= 2 * hsd::kCS) {
+        // narrow sweeps: clusters of kCS CTAs, one per SM, one chunk per cluster that can
+        // be resident at once (a wider sweep runs faster in the independent form)
+        static int active_clusters = 0;
+        const size_t csmem = smem > kOneCtaPerSm ? smem : kOneCtaPerSm;
+        if (configured_coop != csmem) {
+            cudaError_t e = cudaFuncSetAttribute(k_hs_coop<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
+            if (e != cudaSuccess) return e;
+            cudaLaunchConfig_t lc = {};
+            lc.gridDim = dim3((unsigned)((num_sms / hsd::kCS) * hsd::kCS));
+            lc.blockDim = dim3((unsigned)C::NT);
+            lc.dynamicSmemBytes = csmem;
+            int nc = 0;
+            e = cudaOccupancyMaxActiveClusters(&nc, k_hs_coop<N>, &lc);
+            if (e != cudaSuccess) return e;
+            active_clusters = nc;
+            configured_coop = csmem;
+        }
+        if (active_clusters > 0) {
+            coop_max = (long long)active_clusters * C::BB;
+            k_hs_coop<N><<<active_clusters * hsd::kCS, C::NT, csmem, st>>>(a, cache ? 1 : 0, coop_max);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+      }
+    }
     if (per_sm == 0 || configured_smem != smem) {
         cudaError_t e = cudaFuncSetAttribute(k_hs<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -623,7 +786,7 @@ static cudaError_t launch_hs_n(const SweepArgs &a, int num_sms, cudaStream_t st)
         per_sm = bl < 1 ? 1 : bl;
         configured_smem = smem;
     }
-    k_hs<N><<<num_sms * per_sm, C::NT, smem, st>>>(a, cache ? 1 : 0);
+    k_hs<N><<<num_sms * per_sm, C::NT, smem, st>>>(a, cache ? 1 : 0, coop_max);
     return cudaGetLastError();
 }
 

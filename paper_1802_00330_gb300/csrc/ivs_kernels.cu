@@ -356,134 +356,180 @@ __device__ __forceinline__ void push_surv(const SweepArgs &a, WaveCtl *ctl, int 
     }
 }
 
-// One warp per parent (taken from a shared cursor), one lane per child.  Three forms:
-// the FP32 shadow (decides what FP64 would decide with certainty; the undecided rest go
-// to k_eval64), the plain FP32 prefilter (its survivors go to k_eval64), or FP64 only.
+// The children of one parent, evaluated by a group of threads: one warp (GROUP = 32) or
+// the whole block.  r = the thread's rank in the group, G = the group size; every
+// thread of the group runs this with the same pi.  Three forms: the FP32 shadow (decides
+// what FP64 would decide with certainty; the undecided rest go to k_eval64), the plain
+// FP32 prefilter (its survivors go to k_eval64), or FP64 only.
+template <bool BLOCK>
+__device__ __forceinline__ void group_sync() {
+    if (BLOCK) __syncthreads();
+    else __syncwarp();
+}
+
+template <bool BLOCK>
+__device__ __forceinline__ void eval_parent(const SweepArgs &a, WaveCtl *ctl, const char *s_blob, float4 *s_tv,
+                                            double (*sp)[kMaxVars], float (*sf)[kMaxVars], float (*se)[kMaxVars],
+                                            int *s_flag, int64_t pi, unsigned r, unsigned G) {
+    const unsigned lane = lane_id();
+    const int sys = a.q.sys[pi];
+    const uint32_t meta = a.q.meta[pi];
+    const DevSys S = a.tb.sys[sys];
+    const SysTab T = make_tab(a.single ? s_blob : a.tb.blobs + S.blob_off, S);
+    const bool root = (meta & kRootFlag) != 0;
+    const int depth = (int)(meta & kDepthMask) + (root ? 0 : 1);
+    // the parent leaves the queue; past the box budget its children are dropped (the
+    // decision of rank 0, shared by the group)
+    int over = 0;
+    if (r == 0) {
+        atomicAdd(stat_ptr(a, sys, ST_LIVE), ~0ull);
+        if (S.max_boxes > 0) {
+            const unsigned long long done = *(volatile unsigned long long *)stat_ptr(a, sys, ST_BOXES);
+            if ((long long)done >= S.max_boxes) {
+                atomicOr(stat_ptr(a, sys, ST_FLAGS), (unsigned long long)kFlagBudget);
+                over = 1;
+            }
+        }
+        if (BLOCK) *s_flag = over;
+    }
+    if (BLOCK) {
+        __syncthreads();
+        over = *s_flag;
+    } else {
+        over = __shfl_sync(kFull, over, 0);
+    }
+    if (over) {
+        if (BLOCK) __syncthreads();   // s_flag is rewritten for the next parent
+        return;
+    }
+    const int n = S.n;
+    if ((int)r < n) {
+        const double lo = a.q.lo[r * a.q.cap + pi];
+        const double mid = a.q.mid[r * a.q.cap + pi];
+        const double hi = a.q.hi[r * a.q.cap + pi];
+        sp[0][r] = lo;
+        sp[1][r] = mid;
+        sp[2][r] = hi;
+        const float lod = __double2float_rd(lo), lou = __double2float_ru(lo);
+        const float mdd = __double2float_rd(mid), mdu = __double2float_ru(mid);
+        const float hid = __double2float_rd(hi), hiu = __double2float_ru(hi);
+        sf[0][r] = lod;
+        sf[1][r] = mdd;
+        sf[2][r] = mdu;
+        sf[3][r] = hiu;
+        se[0][r] = lod;
+        se[1][r] = lou;
+        se[2][r] = mdd;
+        se[3][r] = mdu;
+        se[4][r] = hid;
+        se[5][r] = hiu;
+    }
+    group_sync<BLOCK>();
+    const unsigned fan = root ? 1u : (1u << n);
+    unsigned cnt_pre = 0, cnt_ev = 0, cnt_64 = 0, cnt_sh = 0;
+    // per-parent term-combination table: when the fan-out fills warps and it fits
+    const bool use_tv = S.prefilter && S.shadow && S.n_tv > 0 && S.n_tv <= a.tv_stride && fan >= 32;
+    if (use_tv) {
+        for (int e = (int)r; e < S.n_tv; e += (int)G) {
+            const uint32_t mp = T.tv_map[e];
+            s_tv[e] = term_shadow(T, (int)(mp >> 8), ComboCoordShadow{se, mp & 255u});
+        }
+        group_sync<BLOCK>();
+    }
+    for (unsigned c0 = 0; c0 < fan; c0 += G) {
+        const unsigned c = c0 + r;
+        const bool active = c < fan;
+        bool keep = false, cand = false;
+        if (active) {
+            if (use_tv) {
+                const int d = decide_from_table(T, S, s_tv, c);
+                keep = d == 1;
+                cand = d == 2;
+                cnt_pre += d == 0 ? 1u : 0u;
+                cnt_sh += keep ? 1u : 0u;
+            } else if (S.prefilter && S.shadow) {
+                const int d = decide_shadow(T, S, ChildCoordShadow{se, c});
+                keep = d == 1;
+                cand = d == 2;
+                cnt_pre += d == 0 ? 1u : 0u;
+                cnt_sh += keep ? 1u : 0u;
+            } else if (S.prefilter) {
+                cand = keep32(T, S, ChildCoord32{sf, c});
+                cnt_pre += cand ? 0u : 1u;
+            } else {
+                cnt_64 += 1;
+                keep = keep64(T, S, ChildCoord64{sp, c});
+                cnt_ev += keep ? 0u : 1u;
+            }
+        }
+        push_surv(a, ctl, n, keep, Surv{(uint32_t)pi, c});
+        const unsigned cm = __ballot_sync(kFull, cand);
+        if (cm) {
+            unsigned long long pos = 0;
+            if (lane == 0) pos = atomicAdd((unsigned long long *)&ctl->cand_count, (unsigned long long)__popc(cm));
+            pos = __shfl_sync(kFull, pos, 0);
+            if (cand) {
+                const unsigned long long k = pos + __popc(cm & lanemask_lt());
+                if ((long long)k < a.surv_cap) a.cand[k] = Surv{(uint32_t)pi, c};
+                else ctl->error = 1;
+            }
+        }
+    }
+    cnt_pre = __reduce_add_sync(kFull, cnt_pre);
+    cnt_ev = __reduce_add_sync(kFull, cnt_ev);
+    cnt_64 = __reduce_add_sync(kFull, cnt_64);
+    cnt_sh = __reduce_add_sync(kFull, cnt_sh);
+    if (lane == 0) {
+        if (r == 0) {
+            atomicAdd(stat_ptr(a, sys, ST_BOXES), (unsigned long long)fan);
+            atomicMax(stat_ptr(a, sys, ST_MAX_DEPTH), (unsigned long long)depth);
+        }
+        if (cnt_pre) atomicAdd(stat_ptr(a, sys, ST_EXCL_PREFILTER), (unsigned long long)cnt_pre);
+        if (cnt_ev) atomicAdd(stat_ptr(a, sys, ST_EXCL_EVAL), (unsigned long long)cnt_ev);
+        if (cnt_64) atomicAdd(stat_ptr(a, sys, ST_EVAL64), (unsigned long long)cnt_64);
+        if (cnt_sh) atomicAdd(stat_ptr(a, sys, ST_KEEP_SHADOW), (unsigned long long)cnt_sh);
+    }
+    group_sync<BLOCK>();   // the parent's arrays are rewritten for the next parent
+}
+
+// Children of the popped parents.  A wide sweep gives each warp a parent at a time from
+// a shared cursor (one lane per child); a narrow one (at most one parent per block)
+// gives each block its parents and spreads a parent's table entries and children over
+// all of the block's threads, so the few parents of the first and last sweeps finish
+// sooner.  Both run the same per-child arithmetic.
 __global__ void __launch_bounds__(kEvalThreads) k_eval(SweepArgs a) {
     extern __shared__ __align__(16) char s_blob[];
-    float4 *s_tv = reinterpret_cast<float4 *>(s_blob + (a.single ? a.blob_smem : 0)) +
-                   (size_t)(threadIdx.x >> 5) * a.tv_stride;
+    float4 *s_tv_base = reinterpret_cast<float4 *>(s_blob + (a.single ? a.blob_smem : 0));
     __shared__ double s_p[kEvalWarps][3][kMaxVars];
     __shared__ float s_f[kEvalWarps][4][kMaxVars];
     __shared__ float s_e[kEvalWarps][6][kMaxVars];
+    __shared__ int s_flag;
     const unsigned lane = lane_id();
     const int w = threadIdx.x >> 5;
     WaveCtl *ctl = a.ctl;
     const int64_t base = ctl->base, K = ctl->k;
-    // blocks beyond what K parents need leave at once (the others take every parent
-    // from the shared cursor), so a small sweep does not pay for the whole grid
-    if ((int64_t)blockIdx.x * (blockDim.x >> 5) >= K) return;
+    const bool block_mode = K <= (int64_t)gridDim.x;
+    // blocks beyond what K parents need leave at once (the others take every parent), so
+    // a small sweep does not pay for the whole grid
+    if (block_mode ? (int64_t)blockIdx.x >= K : (int64_t)blockIdx.x * (blockDim.x >> 5) >= K) return;
     if (a.single) {
         const DevSys &S0 = a.tb.sys[0];
         copy_blob(s_blob, a.tb.blobs + S0.blob_off, (uint32_t)S0.blob_bytes);
         __syncthreads();
     }
+    if (block_mode) {
+        for (int64_t p = blockIdx.x; p < K; p += gridDim.x)
+            eval_parent<true>(a, ctl, s_blob, s_tv_base, s_p[0], s_f[0], s_e[0], &s_flag, base + p, threadIdx.x,
+                              blockDim.x);
+        return;
+    }
+    float4 *s_tv = s_tv_base + (size_t)w * a.tv_stride;
     for (;;) {
         int p = 0;
         if (lane == 0) p = atomicAdd(&ctl->cursor, 1);
         p = __shfl_sync(kFull, p, 0);
         if (p >= K) break;
-        const int64_t pi = base + p;
-        const int sys = a.q.sys[pi];
-        const uint32_t meta = a.q.meta[pi];
-        const DevSys S = a.tb.sys[sys];
-        const SysTab T = make_tab(a.single ? s_blob : a.tb.blobs + S.blob_off, S);
-        const bool root = (meta & kRootFlag) != 0;
-        const int depth = (int)(meta & kDepthMask) + (root ? 0 : 1);
-        if (lane == 0) atomicAdd(stat_ptr(a, sys, ST_LIVE), ~0ull);   // the parent leaves the queue
-        if (S.max_boxes > 0) {
-            unsigned long long done = *(volatile unsigned long long *)stat_ptr(a, sys, ST_BOXES);
-            if ((long long)done >= S.max_boxes) {
-                if (lane == 0) atomicOr(stat_ptr(a, sys, ST_FLAGS), (unsigned long long)kFlagBudget);
-                continue;
-            }
-        }
-        const int n = S.n;
-        if ((int)lane < n) {
-            const double lo = a.q.lo[lane * a.q.cap + pi];
-            const double mid = a.q.mid[lane * a.q.cap + pi];
-            const double hi = a.q.hi[lane * a.q.cap + pi];
-            s_p[w][0][lane] = lo;
-            s_p[w][1][lane] = mid;
-            s_p[w][2][lane] = hi;
-            const float lod = __double2float_rd(lo), lou = __double2float_ru(lo);
-            const float mdd = __double2float_rd(mid), mdu = __double2float_ru(mid);
-            const float hid = __double2float_rd(hi), hiu = __double2float_ru(hi);
-            s_f[w][0][lane] = lod;
-            s_f[w][1][lane] = mdd;
-            s_f[w][2][lane] = mdu;
-            s_f[w][3][lane] = hiu;
-            s_e[w][0][lane] = lod;
-            s_e[w][1][lane] = lou;
-            s_e[w][2][lane] = mdd;
-            s_e[w][3][lane] = mdu;
-            s_e[w][4][lane] = hid;
-            s_e[w][5][lane] = hiu;
-        }
-        __syncwarp();
-        const unsigned fan = root ? 1u : (1u << n);
-        unsigned cnt_pre = 0, cnt_ev = 0, cnt_64 = 0, cnt_sh = 0;
-        // per-parent term-combination table: when the fan-out fills warps and it fits
-        const bool use_tv = S.prefilter && S.shadow && S.n_tv > 0 && S.n_tv <= a.tv_stride && fan >= 32;
-        if (use_tv) {
-            for (int e = (int)lane; e < S.n_tv; e += 32) {
-                const uint32_t mp = T.tv_map[e];
-                s_tv[e] = term_shadow(T, (int)(mp >> 8), ComboCoordShadow{s_e[w], mp & 255u});
-            }
-            __syncwarp();
-        }
-        for (unsigned c0 = 0; c0 < fan; c0 += 32) {
-            const unsigned c = c0 + lane;
-            const bool active = c < fan;
-            bool keep = false, cand = false;
-            if (active) {
-                if (use_tv) {
-                    const int r = decide_from_table(T, S, s_tv, c);
-                    keep = r == 1;
-                    cand = r == 2;
-                    cnt_pre += r == 0 ? 1u : 0u;
-                    cnt_sh += keep ? 1u : 0u;
-                } else if (S.prefilter && S.shadow) {
-                    const int r = decide_shadow(T, S, ChildCoordShadow{s_e[w], c});
-                    keep = r == 1;
-                    cand = r == 2;
-                    cnt_pre += r == 0 ? 1u : 0u;
-                    cnt_sh += keep ? 1u : 0u;
-                } else if (S.prefilter) {
-                    cand = keep32(T, S, ChildCoord32{s_f[w], c});
-                    cnt_pre += cand ? 0u : 1u;
-                } else {
-                    cnt_64 += 1;
-                    keep = keep64(T, S, ChildCoord64{s_p[w], c});
-                    cnt_ev += keep ? 0u : 1u;
-                }
-            }
-            push_surv(a, ctl, n, keep, Surv{(uint32_t)pi, c});
-            const unsigned cm = __ballot_sync(kFull, cand);
-            if (cm) {
-                unsigned long long pos = 0;
-                if (lane == 0) pos = atomicAdd((unsigned long long *)&ctl->cand_count, (unsigned long long)__popc(cm));
-                pos = __shfl_sync(kFull, pos, 0);
-                if (cand) {
-                    const unsigned long long k = pos + __popc(cm & lanemask_lt());
-                    if ((long long)k < a.surv_cap) a.cand[k] = Surv{(uint32_t)pi, c};
-                    else ctl->error = 1;
-                }
-            }
-        }
-        cnt_pre = __reduce_add_sync(kFull, cnt_pre);
-        cnt_ev = __reduce_add_sync(kFull, cnt_ev);
-        cnt_64 = __reduce_add_sync(kFull, cnt_64);
-        cnt_sh = __reduce_add_sync(kFull, cnt_sh);
-        if (lane == 0) {
-            atomicAdd(stat_ptr(a, sys, ST_BOXES), (unsigned long long)fan);
-            if (cnt_pre) atomicAdd(stat_ptr(a, sys, ST_EXCL_PREFILTER), (unsigned long long)cnt_pre);
-            if (cnt_ev) atomicAdd(stat_ptr(a, sys, ST_EXCL_EVAL), (unsigned long long)cnt_ev);
-            if (cnt_64) atomicAdd(stat_ptr(a, sys, ST_EVAL64), (unsigned long long)cnt_64);
-            if (cnt_sh) atomicAdd(stat_ptr(a, sys, ST_KEEP_SHADOW), (unsigned long long)cnt_sh);
-            atomicMax(stat_ptr(a, sys, ST_MAX_DEPTH), (unsigned long long)depth);
-        }
-        __syncwarp();
+        eval_parent<false>(a, ctl, s_blob, s_tv, s_p[w], s_f[w], s_e[w], &s_flag, base + p, lane, 32u);
     }
 }
 
