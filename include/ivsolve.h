@@ -261,6 +261,31 @@ int ivs_server_get_stats(ivs_server *sv, ivs_server_stats *st);
 /* Stops the worker (requests not finished are dropped) and frees everything. */
 void ivs_server_destroy(ivs_server *sv);
 
+/* ---- root isolation and backtracking (after the solve; host only) ---------------- */
+/* Section 3.4: the last round leaves many tiny configurations; merging them isolates the
+ * real roots.  ivs_clusters groups boxes (row-major lo/hi, count x n_vars, any order, e.g.
+ * the boxes of ivs_result_boxes) into the connected components of "touch" (boxes a and b
+ * touch when lo_a,j <= hi_b,j and lo_b,j <= hi_a,j for every j); the boxes around one
+ * isolated real root form one component, also when the root sits on split planes and its
+ * boxes lie on several sides of them.  Writes the number of clusters; label[i] = cluster of
+ * box i, clusters numbered in the order of their first box (NULL to skip); for the first
+ * cl_cap clusters their hull in cl_lo / cl_hi (n_vars doubles each; NULL to skip).  A sweep
+ * over the first coordinate: work grows with the pairs of boxes whose first coordinates
+ * overlap; IVS_ERR_BUDGET beyond 4e9 such pairs.  No GPU needed. */
+int ivs_clusters(int32_t n_vars, int64_t count, const double *lo, const double *hi, int64_t *n_clusters,
+                 int64_t *label, double *cl_lo, double *cl_hi, int64_t cl_cap);
+/* Algorithm 5 (backtracking a configuration to the round before), read on the dyadic grid
+ * of the initial box [box_lo, box_hi] and applied `level` rounds up from the finest: the
+ * number of distinct cells of that grid at level `level` (cell width (box_hi_j - box_lo_j) /
+ * 2^level) that the boxes meet -- the "backtracking boxes" the paper tabulates per width.
+ * Per coordinate t = (x - box_lo_j) / width in round to nearest (exact for dyadic data), a
+ * box meets cells floor(t_lo) .. ceil(t_hi) - 1, the two ends swapped when they cross (a
+ * box of width 0 on a cell boundary meets both cells), clamped to the grid.  A root on a
+ * cell corner gives several cells here and one cluster in ivs_clusters.  IVS_ERR_BUDGET if
+ * more than max_cells cells would be enumerated.  No GPU needed. */
+int ivs_backtrack(int32_t n_vars, int64_t count, const double *lo, const double *hi, const double *box_lo,
+                  const double *box_hi, int32_t level, int64_t max_cells, int64_t *n_cells);
+
 /* ---- allocation-free solve ------------------------------------------------------ */
 /* No counterpart in the paper: an entry point for callers that cannot allocate.  Code
  * that runs while a CUDA stream is being captured into a graph, processes whose device

@@ -84,6 +84,10 @@ def _load():
             lib.orc_gj_inverse.argtypes = [C.c_int, vp, vp]
             lib.orc_hs_step.argtypes = [C.POINTER(_Sys), vp, vp, vp, vp]
             lib.orc_centred.argtypes = [C.POINTER(_Sys), vp, vp, vp, vp]
+            lib.orc_clusters.argtypes = [C.c_int, C.c_int64, vp, vp, vp]
+            lib.orc_clusters.restype = C.c_int64
+            lib.orc_backtrack.argtypes = [C.c_int, C.c_int64, vp, vp, vp, vp, C.c_int, C.c_int64]
+            lib.orc_backtrack.restype = C.c_int64
             _lib = lib
     return _lib
 
@@ -225,3 +229,27 @@ def centred(s, lo, hi):
     oh = np.zeros(s.n_eqs)
     lib.orc_centred(C.byref(h.c), _ptr(lo), _ptr(hi), _ptr(ol), _ptr(oh))
     return ol, oh
+
+
+def clusters(lo, hi):
+    """Connected components of touching boxes (rows of lo/hi).  Returns (count, labels)."""
+    lib = _load()
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    k, n = lo.shape if lo.ndim == 2 else (0, 1)
+    labels = np.zeros(max(k, 1), np.int64)
+    nc = lib.orc_clusters(int(n), int(k), _ptr(lo), _ptr(hi), _ptr(labels))
+    return int(nc), labels[:k]
+
+
+def backtrack(lo, hi, d_lo, d_hi, level, max_cells=1 << 26):
+    """Distinct cells of `level` of the initial box's dyadic grid met by the boxes
+    (Algorithm 5 read on that grid); -1 if more than max_cells would be enumerated."""
+    lib = _load()
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    d_lo = np.ascontiguousarray(d_lo, dtype=np.float64)
+    d_hi = np.ascontiguousarray(d_hi, dtype=np.float64)
+    k, n = lo.shape if lo.ndim == 2 else (0, len(d_lo))
+    return int(lib.orc_backtrack(int(n), int(k), _ptr(lo), _ptr(hi), _ptr(d_lo), _ptr(d_hi), int(level),
+                                 int(max_cells)))

@@ -793,3 +793,102 @@ void orc_eval_f32(const orc_system *s, const double *lo, const double *hi, float
         out_hi[i] = acc.hi;
     }
 }
+
+
+/* ---- root isolation and backtracking (post-processing of a result) ---------------- */
+
+static int64_t uf_find(int64_t *par, int64_t a) {
+    while (par[a] != a) a = par[a];
+    return a;
+}
+
+static int boxes_touch(int n, const double *lo, const double *hi, int64_t a, int64_t b) {
+    for (int j = 0; j < n; j++)
+        if (!(lo[a * n + j] <= hi[b * n + j] && lo[b * n + j] <= hi[a * n + j])) return 0;
+    return 1;
+}
+
+int64_t orc_clusters(int n, int64_t count, const double *lo, const double *hi, int64_t *label) {
+    if (count <= 0) return 0;
+    int64_t *par = (int64_t *)malloc(sizeof(int64_t) * (size_t)count);
+    if (!par) return -1;
+    for (int64_t i = 0; i < count; i++) par[i] = i;
+    for (int64_t i = 0; i < count; i++)
+        for (int64_t k = i + 1; k < count; k++)
+            if (boxes_touch(n, lo, hi, i, k)) {
+                int64_t a = uf_find(par, i), b = uf_find(par, k);
+                if (a != b) par[a < b ? b : a] = a < b ? a : b;   /* root = smallest index */
+            }
+    /* number the clusters in the order of their first (smallest) box */
+    int64_t nc = 0;
+    int64_t *num = (int64_t *)malloc(sizeof(int64_t) * (size_t)count);
+    if (!num) { free(par); return -1; }
+    for (int64_t i = 0; i < count; i++) num[i] = -1;
+    for (int64_t i = 0; i < count; i++) {
+        int64_t r = uf_find(par, i);
+        if (num[r] < 0) num[r] = nc++;
+        label[i] = num[r];
+    }
+    free(num);
+    free(par);
+    return nc;
+}
+
+static int cmp_cells_n;
+static int cmp_cells(const void *pa, const void *pb) {
+    const int32_t *a = (const int32_t *)pa, *b = (const int32_t *)pb;
+    for (int j = 0; j < cmp_cells_n; j++) {
+        if (a[j] < b[j]) return -1;
+        if (a[j] > b[j]) return 1;
+    }
+    return 0;
+}
+
+int64_t orc_backtrack(int n, int64_t count, const double *lo, const double *hi, const double *d_lo,
+                      const double *d_hi, int level, int64_t max_cells) {
+    const int64_t side = (int64_t)1 << level;
+    int64_t total = 0, cap = 0;
+    int32_t *cells = NULL;
+    int32_t a[16], b[16], cur[16];
+    for (int64_t i = 0; i < count; i++) {
+        int64_t m = 1;
+        for (int j = 0; j < n; j++) {
+            double w = ldexp(d_hi[j] - d_lo[j], -level);
+            double tl = (lo[i * n + j] - d_lo[j]) / w, th = (hi[i * n + j] - d_lo[j]) / w;
+            double fa = floor(tl), fb = ceil(th) - 1.0;
+            double x = fa < fb ? fa : fb, y = fa < fb ? fb : fa;
+            if (x < 0) x = 0;
+            if (y > (double)(side - 1)) y = (double)(side - 1);
+            if (y < x) y = x;   /* a box outside the grid: the nearest cell */
+            if (x > (double)(side - 1)) x = y = (double)(side - 1);
+            a[j] = (int32_t)x;
+            b[j] = (int32_t)y;
+            m *= (int64_t)(b[j] - a[j] + 1);
+            if (m > max_cells) { free(cells); return -1; }
+        }
+        if (total + m > max_cells) { free(cells); return -1; }
+        if (total + m > cap) {
+            int64_t nc = (total + m) * 2;
+            int32_t *nb = (int32_t *)realloc(cells, sizeof(int32_t) * (size_t)(nc * n));
+            if (!nb) { free(cells); return -1; }
+            cells = nb;
+            cap = nc;
+        }
+        for (int j = 0; j < n; j++) cur[j] = a[j];
+        for (int64_t q = 0; q < m; q++) {   /* odometer over the box's cell ranges */
+            memcpy(cells + (size_t)(total * n), cur, sizeof(int32_t) * (size_t)n);
+            total++;
+            for (int j = 0; j < n; j++) {
+                if (cur[j] < b[j]) { cur[j]++; break; }
+                cur[j] = a[j];
+            }
+        }
+    }
+    cmp_cells_n = n;
+    if (total > 1) qsort(cells, (size_t)total, sizeof(int32_t) * (size_t)n, cmp_cells);
+    int64_t distinct = 0;
+    for (int64_t i = 0; i < total; i++)
+        if (i == 0 || cmp_cells(cells + (size_t)((i - 1) * n), cells + (size_t)(i * n)) != 0) distinct++;
+    free(cells);
+    return distinct;
+}

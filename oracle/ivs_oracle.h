@@ -101,6 +101,18 @@ int orc_gj_inverse(int n, const double *a, double *inv);
 /* one Hansen-Sengupta sweep (Section 2.3, Algorithm 3):
  * returns 0 = box out (maybe unchanged), 1 = empty, 2 = skipped (singular) */
 int orc_hs_step(const orc_system *sys, const double *lo, const double *hi, double *out_lo, double *out_hi);
+/* Root isolation over a set of boxes (row-major lo/hi, count x n): clusters are the
+ * connected components of "touch" (two boxes touch when lo_j <= hi'_j and lo'_j <= hi_j for
+ * every j).  label[i] = cluster of box i, clusters numbered in the order of their first box.
+ * Returns the number of clusters.  Plain O(count^2) union-find. */
+int64_t orc_clusters(int n, int64_t count, const double *lo, const double *hi, int64_t *label);
+/* Backtracking (Algorithm 5, read on the dyadic grid of the initial box): the number of
+ * distinct cells of level `level` (cell width (d_hi - d_lo) / 2^level per coordinate) that
+ * the boxes meet; per coordinate t = (x - d_lo) / w in round to nearest, cells from
+ * floor(t_lo) to ceil(t_hi) - 1 (the two ends swapped when they cross), clamped to the grid.
+ * Returns -1 when more than max_cells cells would be enumerated. */
+int64_t orc_backtrack(int n, int64_t count, const double *lo, const double *hi, const double *d_lo,
+                      const double *d_hi, int level, int64_t max_cells);
 /* centred form of every equation over the box (n_eqs == n_vars): out[i] = F_c,i(X) */
 void orc_centred(const orc_system *sys, const double *lo, const double *hi, double *out_lo, double *out_hi);
 

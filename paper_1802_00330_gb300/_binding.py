@@ -71,6 +71,9 @@ _PP = C.POINTER(C.c_void_p)
 SIGNATURES = {
     "ivs_options_default": (None, [C.POINTER(ivs_options)]),
     "ivs_release_cached": (None, []),
+    "ivs_clusters": (C.c_int, [C.c_int32, C.c_int64, _VP, _VP, C.POINTER(C.c_int64), _VP, _VP, _VP, C.c_int64]),
+    "ivs_backtrack": (C.c_int, [C.c_int32, C.c_int64, _VP, _VP, _VP, _VP, C.c_int32, C.c_int64,
+                                C.POINTER(C.c_int64)]),
     "ivs_solve": (C.c_int, [C.POINTER(ivs_system), _VP, _VP, C.POINTER(ivs_options), _PP]),
     "ivs_solve_batch": (C.c_int, [C.c_int32, C.POINTER(ivs_system), _VP, _VP, C.POINTER(ivs_options),
                                   C.c_int32, _PP]),
@@ -401,3 +404,36 @@ def solve_batch(systems, **opts):
 def release_cached():
     """Frees the device memory, stream and graph that ivs_solve keeps from its last call."""
     load().ivs_release_cached()
+
+
+def clusters(lo, hi, with_hulls=True):
+    """Isolated roots of a box set (rows of lo/hi): connected components of touching boxes
+    through ``ivs_clusters``.  Returns (count, labels, hull_lo, hull_hi)."""
+    lib = load()
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    k = lo.shape[0]
+    n = lo.shape[1] if lo.ndim == 2 and k else 1
+    nc = C.c_int64()
+    labels = np.zeros(max(k, 1), np.int64)
+    hl = np.zeros((max(k, 1), n))
+    hh = np.zeros((max(k, 1), n))
+    _check(lib.ivs_clusters(n, k, _ptr(lo), _ptr(hi), C.byref(nc), _ptr(labels),
+                            _ptr(hl) if with_hulls else None, _ptr(hh) if with_hulls else None, k))
+    c = nc.value
+    return c, labels[:k], hl[:c], hh[:c]
+
+
+def backtrack(lo, hi, box_lo, box_hi, level, max_cells=1 << 26):
+    """Distinct cells of `level` of the initial box's dyadic grid met by the boxes
+    (Algorithm 5 read on that grid) through ``ivs_backtrack``."""
+    lib = load()
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    bl = np.ascontiguousarray(box_lo, dtype=np.float64)
+    bh = np.ascontiguousarray(box_hi, dtype=np.float64)
+    k = lo.shape[0]
+    out = C.c_int64()
+    _check(lib.ivs_backtrack(len(bl), k, _ptr(lo), _ptr(hi), _ptr(bl), _ptr(bh), int(level), int(max_cells),
+                             C.byref(out)))
+    return out.value
