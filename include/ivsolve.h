@@ -281,10 +281,13 @@ int ivs_clusters(int32_t n_vars, int64_t count, const double *lo, const double *
  * Per coordinate t = (x - box_lo_j) / width in round to nearest (exact for dyadic data), a
  * box meets cells floor(t_lo) .. ceil(t_hi) - 1, the two ends swapped when they cross (a
  * box of width 0 on a cell boundary meets both cells), clamped to the grid.  A root on a
- * cell corner gives several cells here and one cluster in ivs_clusters.  IVS_ERR_BUDGET if
- * more than max_cells cells would be enumerated.  No GPU needed. */
+ * cell corner gives several cells.  *n_groups (NULL to skip) receives the connected
+ * components of those cells, cells touching when their indices differ by at most 1 in
+ * every coordinate: the roots isolated at that width (the paper's "N real interval roots,
+ * width w").  IVS_ERR_BUDGET if more than max_cells cells would be enumerated.  No GPU
+ * needed. */
 int ivs_backtrack(int32_t n_vars, int64_t count, const double *lo, const double *hi, const double *box_lo,
-                  const double *box_hi, int32_t level, int64_t max_cells, int64_t *n_cells);
+                  const double *box_hi, int32_t level, int64_t max_cells, int64_t *n_cells, int64_t *n_groups);
 
 /* ---- allocation-free solve ------------------------------------------------------ */
 /* No counterpart in the paper: an entry point for callers that cannot allocate.  Code

@@ -86,7 +86,7 @@ def _load():
             lib.orc_centred.argtypes = [C.POINTER(_Sys), vp, vp, vp, vp]
             lib.orc_clusters.argtypes = [C.c_int, C.c_int64, vp, vp, vp]
             lib.orc_clusters.restype = C.c_int64
-            lib.orc_backtrack.argtypes = [C.c_int, C.c_int64, vp, vp, vp, vp, C.c_int, C.c_int64]
+            lib.orc_backtrack.argtypes = [C.c_int, C.c_int64, vp, vp, vp, vp, C.c_int, C.c_int64, vp]
             lib.orc_backtrack.restype = C.c_int64
             _lib = lib
     return _lib
@@ -242,14 +242,17 @@ def clusters(lo, hi):
     return int(nc), labels[:k]
 
 
-def backtrack(lo, hi, d_lo, d_hi, level, max_cells=1 << 26):
+def backtrack(lo, hi, d_lo, d_hi, level, max_cells=1 << 26, groups=False):
     """Distinct cells of `level` of the initial box's dyadic grid met by the boxes
-    (Algorithm 5 read on that grid); -1 if more than max_cells would be enumerated."""
+    (Algorithm 5 read on that grid); -1 if more than max_cells would be enumerated.
+    With groups=True returns (cells, connected components of the cells)."""
     lib = _load()
     lo = np.ascontiguousarray(lo, dtype=np.float64)
     hi = np.ascontiguousarray(hi, dtype=np.float64)
     d_lo = np.ascontiguousarray(d_lo, dtype=np.float64)
     d_hi = np.ascontiguousarray(d_hi, dtype=np.float64)
     k, n = lo.shape if lo.ndim == 2 else (0, len(d_lo))
-    return int(lib.orc_backtrack(int(n), int(k), _ptr(lo), _ptr(hi), _ptr(d_lo), _ptr(d_hi), int(level),
-                                 int(max_cells)))
+    g = np.zeros(1, np.int64)
+    c = int(lib.orc_backtrack(int(n), int(k), _ptr(lo), _ptr(hi), _ptr(d_lo), _ptr(d_hi), int(level),
+                              int(max_cells), _ptr(g)))
+    return (c, int(g[0])) if groups else c

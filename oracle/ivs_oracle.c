@@ -845,7 +845,7 @@ static int cmp_cells(const void *pa, const void *pb) {
 }
 
 int64_t orc_backtrack(int n, int64_t count, const double *lo, const double *hi, const double *d_lo,
-                      const double *d_hi, int level, int64_t max_cells) {
+                      const double *d_hi, int level, int64_t max_cells, int64_t *groups) {
     const int64_t side = (int64_t)1 << level;
     int64_t total = 0, cap = 0;
     int32_t *cells = NULL;
@@ -864,13 +864,13 @@ int64_t orc_backtrack(int n, int64_t count, const double *lo, const double *hi, 
             a[j] = (int32_t)x;
             b[j] = (int32_t)y;
             m *= (int64_t)(b[j] - a[j] + 1);
-            if (m > max_cells) { free(cells); return -1; }
+            if (m > max_cells) { free(cells); if (groups) *groups = -1; return -1; }
         }
-        if (total + m > max_cells) { free(cells); return -1; }
+        if (total + m > max_cells) { free(cells); if (groups) *groups = -1; return -1; }
         if (total + m > cap) {
             int64_t nc = (total + m) * 2;
             int32_t *nb = (int32_t *)realloc(cells, sizeof(int32_t) * (size_t)(nc * n));
-            if (!nb) { free(cells); return -1; }
+            if (!nb) { free(cells); if (groups) *groups = -1; return -1; }
             cells = nb;
             cap = nc;
         }
@@ -888,7 +888,24 @@ int64_t orc_backtrack(int n, int64_t count, const double *lo, const double *hi, 
     if (total > 1) qsort(cells, (size_t)total, sizeof(int32_t) * (size_t)n, cmp_cells);
     int64_t distinct = 0;
     for (int64_t i = 0; i < total; i++)
-        if (i == 0 || cmp_cells(cells + (size_t)((i - 1) * n), cells + (size_t)(i * n)) != 0) distinct++;
+        if (i == 0 || cmp_cells(cells + (size_t)((i - 1) * n), cells + (size_t)(i * n)) != 0) {
+            if (distinct != i) memcpy(cells + (size_t)(distinct * n), cells + (size_t)(i * n), sizeof(int32_t) * (size_t)n);
+            distinct++;
+        }
+    if (groups) {
+        /* cells touch when their indices differ by at most 1 in every coordinate: as the
+         * closed unit boxes [i, i + 1] of index space */
+        double *ul = (double *)malloc(sizeof(double) * (size_t)(distinct * n + 1));
+        double *uh = (double *)malloc(sizeof(double) * (size_t)(distinct * n + 1));
+        int64_t *lab = (int64_t *)malloc(sizeof(int64_t) * (size_t)(distinct + 1));
+        if (!ul || !uh || !lab) {
+            *groups = -1;
+        } else {
+            for (int64_t i = 0; i < distinct * n; i++) { ul[i] = (double)cells[i]; uh[i] = (double)cells[i] + 1.0; }
+            *groups = orc_clusters(n, distinct, ul, uh, lab);
+        }
+        free(ul); free(uh); free(lab);
+    }
     free(cells);
     return distinct;
 }

@@ -110,9 +110,11 @@ int64_t orc_clusters(int n, int64_t count, const double *lo, const double *hi, i
  * distinct cells of level `level` (cell width (d_hi - d_lo) / 2^level per coordinate) that
  * the boxes meet; per coordinate t = (x - d_lo) / w in round to nearest, cells from
  * floor(t_lo) to ceil(t_hi) - 1 (the two ends swapped when they cross), clamped to the grid.
+ * *groups (if not NULL) = connected components of those cells, cells touching when their
+ * indices differ by at most 1 in every coordinate (the roots isolated at that width).
  * Returns -1 when more than max_cells cells would be enumerated. */
 int64_t orc_backtrack(int n, int64_t count, const double *lo, const double *hi, const double *d_lo,
-                      const double *d_hi, int level, int64_t max_cells);
+                      const double *d_hi, int level, int64_t max_cells, int64_t *groups);
 /* centred form of every equation over the box (n_eqs == n_vars): out[i] = F_c,i(X) */
 void orc_centred(const orc_system *sys, const double *lo, const double *hi, double *out_lo, double *out_hi);
 

@@ -73,7 +73,7 @@ SIGNATURES = {
     "ivs_release_cached": (None, []),
     "ivs_clusters": (C.c_int, [C.c_int32, C.c_int64, _VP, _VP, C.POINTER(C.c_int64), _VP, _VP, _VP, C.c_int64]),
     "ivs_backtrack": (C.c_int, [C.c_int32, C.c_int64, _VP, _VP, _VP, _VP, C.c_int32, C.c_int64,
-                                C.POINTER(C.c_int64)]),
+                                C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "ivs_solve": (C.c_int, [C.POINTER(ivs_system), _VP, _VP, C.POINTER(ivs_options), _PP]),
     "ivs_solve_batch": (C.c_int, [C.c_int32, C.POINTER(ivs_system), _VP, _VP, C.POINTER(ivs_options),
                                   C.c_int32, _PP]),
@@ -424,9 +424,10 @@ def clusters(lo, hi, with_hulls=True):
     return c, labels[:k], hl[:c], hh[:c]
 
 
-def backtrack(lo, hi, box_lo, box_hi, level, max_cells=1 << 26):
+def backtrack(lo, hi, box_lo, box_hi, level, max_cells=1 << 26, groups=False):
     """Distinct cells of `level` of the initial box's dyadic grid met by the boxes
-    (Algorithm 5 read on that grid) through ``ivs_backtrack``."""
+    (Algorithm 5 read on that grid) through ``ivs_backtrack``; with groups=True also the
+    connected components of those cells (the roots isolated at that width)."""
     lib = load()
     lo = np.ascontiguousarray(lo, dtype=np.float64)
     hi = np.ascontiguousarray(hi, dtype=np.float64)
@@ -434,6 +435,7 @@ def backtrack(lo, hi, box_lo, box_hi, level, max_cells=1 << 26):
     bh = np.ascontiguousarray(box_hi, dtype=np.float64)
     k = lo.shape[0]
     out = C.c_int64()
+    grp = C.c_int64()
     _check(lib.ivs_backtrack(len(bl), k, _ptr(lo), _ptr(hi), _ptr(bl), _ptr(bh), int(level), int(max_cells),
-                             C.byref(out)))
-    return out.value
+                             C.byref(out), C.byref(grp)))
+    return (out.value, grp.value) if groups else out.value

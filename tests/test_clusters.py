@@ -37,11 +37,14 @@ def test_clusters_equal_oracle(lib, orc, n, k, seed):
 
 @pytest.mark.parametrize("level", [0, 1, 3, 6, 10])
 def test_backtrack_equals_oracle(lib, orc, level):
+    """Random boxes of 0 to ~3 cells per coordinate at the level, anywhere in the box."""
     rng = random.Random(200 + level)
     d_lo, d_hi = np.array([-4.0, -1.0, 0.0, -32.0]), np.array([4.0, 1.0, 2.0, 32.0])
+    cw = (d_hi - d_lo) / 2 ** level
     lo = np.array([[rng.uniform(a, b) for a, b in zip(d_lo, d_hi)] for _ in range(300)])
-    hi = lo + np.array([[rng.choice([0.0, 1e-3, 0.01, 0.3]) for _ in range(4)] for _ in range(300)])
-    assert lib.backtrack(lo, hi, d_lo, d_hi, level) == orc.backtrack(lo, hi, d_lo, d_hi, level)
+    hi = lo + np.array([[rng.choice([0.0, 0.01, 0.5, 2.5]) * cw[j] for j in range(4)] for _ in range(300)])
+    assert lib.backtrack(lo, hi, d_lo, d_hi, level, groups=True) == orc.backtrack(lo, hi, d_lo, d_hi, level,
+                                                                                  groups=True)
 
 
 def test_on_solver_output(lib, orc):
@@ -54,8 +57,8 @@ def test_on_solver_output(lib, orc):
         oc, olabels = orc.clusters(r["lo"], r["hi"])
         assert c == oc and np.array_equal(labels, olabels)
         for level in (2, 5, 9):
-            assert lib.backtrack(r["lo"], r["hi"], s.box_lo, s.box_hi, level) == \
-                orc.backtrack(r["lo"], r["hi"], s.box_lo, s.box_hi, level)
+            assert lib.backtrack(r["lo"], r["hi"], s.box_lo, s.box_hi, level, groups=True) == \
+                orc.backtrack(r["lo"], r["hi"], s.box_lo, s.box_hi, level, groups=True)
 
 
 def test_empty_and_invalid(lib):
@@ -65,18 +68,23 @@ def test_empty_and_invalid(lib):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("name,roots,level", [("noon9", 19, 8), ("kinema", 8, 11)])
-def test_paper_root_counts(lib, orc, name, roots, level):
-    """The paper's printed systems solved on the GPU with HS from the first round: the
-    accepted boxes form exactly the paper's number of isolated real roots (Section 4,
-    Tables 6 and 8), and the oracle's clustering of the same boxes agrees."""
+@pytest.mark.parametrize("name,roots,widths", [("noon9", 19, (8, 7)), ("kinema", 8, (11, 10))])
+def test_paper_root_counts(lib, orc, name, roots, widths):
+    """The paper's printed systems solved on the GPU with HS from the first round, then
+    backtracked (Algorithm 5) to the widths the paper reports and merged: exactly the
+    paper's number of isolated real roots at both widths (Section 4: noon9 19 roots at
+    width 0.0625 and 0.125, Table 6; kinema 8 roots at width 0.03125 and 0.0625, Table 8),
+    the same as the oracle's backtracking of the same boxes."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     s = synth.load_fixture(f"tests/golden/{name}.txt")
     r = lib.solve(s, tol=1e-3)
     assert r["status"] == 0
-    c, labels, hl, hh = lib.clusters(r["lo"], r["hi"])
-    assert c == roots
-    assert orc.clusters(r["lo"], r["hi"])[0] == roots
-    assert np.all(hh - hl < (s.box_hi - s.box_lo) / 2 ** level)   # each root isolated below the paper's width
+    for level in widths:
+        cells, groups = lib.backtrack(r["lo"], r["hi"], s.box_lo, s.box_hi, level, groups=True)
+        assert groups == roots, (level, cells, groups)
+        assert orc.backtrack(r["lo"], r["hi"], s.box_lo, s.box_hi, level, groups=True) == (cells, groups)
+    if name == "kinema":
+        # kinema's roots are also separated as touching components of the boxes themselves
+        assert lib.clusters(r["lo"], r["hi"])[0] == roots

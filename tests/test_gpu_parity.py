@@ -104,6 +104,16 @@ def test_paper_round_counts_on_gpu(gpu):
         assert int(np.sum((g["flags"] & 4) == 4)) == want
 
 
+def test_paper_round_counts_deeper_on_gpu(gpu):
+    """Deeper rounds the oracle is too slow for: katsura8 round 4 (92,880, Table 1) and
+    kinema rounds 5-6 (407,380 and 4,369,735, Table 7), without HS."""
+    for name, depth, want in (("katsura8", 3, 92880), ("kinema", 4, 407380), ("kinema", 5, 4369735)):
+        s = synth.load_fixture(os.path.join(GOLDEN, f"{name}.txt"))
+        g = gpu.solve(s, hs_enable=0, tol=0.0, max_depth=depth, max_results=1 << 23)
+        assert g["status"] == 3
+        assert int(np.sum((g["flags"] & 4) == 4)) == want
+
+
 def test_edge_cases(gpu, orc):
     # root-free system: empty result, OK
     s = synth.parse_system(["x1^2 + x2^2 + 1", "x1 - x2"], 2, box=(-3, 3), tol=1e-6)
