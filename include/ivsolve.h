@@ -212,18 +212,16 @@ int ivs_probe_rate(int32_t kind, int32_t device, double *ops_per_s, double *ms);
 /* A server keeps one device-resident queue for every system in flight.  Requests that
  * arrive while others run are admitted between sweeps (one sweep = Algorithm 2's
  * evaluation of every child of the popped parents, then Algorithm 3 and the accept /
- * split step) as soon as a slot and queue memory are free: a request reserves
- * 64 * 2^n queue entries (reserve_factor scales it), and admission stops while the
- * reservations of the systems in flight would exceed half of the queue.  Their sweeps
- * share kernels with the systems already running.  A system is solved when none of its
+ * split step) as soon as a slot and queue memory are free: each request owns a region of
+ * 64 * 2^n queue entries (reserve_factor scales it), and requests wait, in arrival order,
+ * until one is free.  Every sweep gives each request in flight a fair share of its
+ * children, and their sweeps share kernels.  A system is solved when none of its
  * boxes remain in the queue; its result (the same as ivs_solve's, bit for bit: each box's
  * fate depends only on the box) is then ready for ivs_server_poll / ivs_server_wait.
  * A request whose options set time_budget_s > 0 and that is still unsolved that long
  * after its admission is cancelled between two sweeps: its remaining boxes are removed
- * from the queue at once, and it completes with IVS_ERR_TIMEOUT and the boxes it had
- * accepted so far.  The queue is a stack shared by all requests (depth first keeps its
- * size bounded), so the most recently admitted work runs first; the time budget bounds
- * how long a request can hold the GPU.
+ * from its region at once, and it completes with IVS_ERR_TIMEOUT and the boxes it had
+ * accepted so far.
  * Submissions and polls may come from any host thread; one worker thread drives the GPU. */
 typedef struct ivs_server ivs_server;
 typedef struct ivs_server_cfg {

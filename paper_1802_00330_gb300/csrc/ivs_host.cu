@@ -146,7 +146,7 @@ bool same_args(const SweepArgs &x, const SweepArgs &y) {
            x.surv_cap == y.surv_cap && x.cand == y.cand && x.stats == y.stats &&
            x.wave_children == y.wave_children && x.max_fan_shift == y.max_fan_shift && x.n_sys == y.n_sys &&
            x.single == y.single && x.blob_smem == y.blob_smem && x.tv_stride == y.tv_stride &&
-           x.eval_warps == y.eval_warps;
+           x.eval_warps == y.eval_warps && x.rg.n == y.rg.n;
 }
 
 // Builds a plan.  With `reuse` (a plan that is no longer needed) its stream, events,

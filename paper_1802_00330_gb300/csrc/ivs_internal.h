@@ -99,6 +99,19 @@ struct WaveCtl {
     int64_t children;       // children the current sweep evaluates
 };
 
+// Serving: one queue region per system slot ("device-resident queues admitted by the
+// memory they need").  Slot s owns entries [base[s], base[s] + cap[s]) of the queue.
+// Between sweeps it holds rem[s] + cursor[s] entries; a sweep pops its top k[s] parents
+// (prefix[s] = popped parents of the slots before s), leaving rem[s] below them, and its
+// new parents go on top (cursor[s] counts them).  n == 0: one stack shared by all systems.
+struct DevRegions {
+    int64_t *base, *cap;
+    int64_t *rem;
+    int64_t *prefix;                 // [n + 1]
+    unsigned long long *cursor;
+    int32_t n;
+};
+
 // survivor of the evaluation: parent index in the queue, child index
 struct Surv {
     uint32_t parent;

@@ -37,9 +37,126 @@ __device__ __forceinline__ unsigned long long *stat_ptr(const SweepArgs &a, int 
 // top - K + children <= cap.  One block scans the fan-outs of the top entries.
 constexpr int kBeginThreads = 1024;
 constexpr int kBeginPer = 64;       // entries per thread: a window of 65536 parents
+// Serving with per-system regions: every region with entries gets a fair share of the
+// sweep's W children (at least one parent), limited by what its region can hold in the
+// worst case; slots are served in an order that rotates with the sweep count, and once W
+// is used up the remaining slots wait for the next sweep.  One block.
+__device__ void wave_begin_regions(const SweepArgs &a) {
+    __shared__ long long s_red[kBeginThreads];
+    __shared__ long long s_active, s_total, s_run;
+    const DevRegions &rg = a.rg;
+    WaveCtl *c = a.ctl;
+    const int t = threadIdx.x, S = rg.n;
+    const int64_t waves = c->waves;
+    if (t == 0) { s_active = 0; s_total = 0; s_run = 0; }
+    __syncthreads();
+    // entries each region holds after the last sweep
+    long long act = 0, tot = 0;
+    for (int sl = t; sl < S; sl += kBeginThreads) {
+        const int64_t held = rg.rem[sl] + (int64_t)rg.cursor[sl];
+        rg.rem[sl] = held;
+        rg.cursor[sl] = 0;
+        act += held > 0 ? 1 : 0;
+        tot += held;
+    }
+    atomicAdd((unsigned long long *)&s_active, (unsigned long long)act);
+    atomicAdd((unsigned long long *)&s_total, (unsigned long long)tot);
+    __syncthreads();
+    const long long share = a.wave_children / (s_active > 0 ? s_active : 1);
+    // rotated order: position q serves slot (q + waves) % S; chunks of kBeginThreads slots
+    // are scanned in order with a running total of children
+    for (int q0 = 0; q0 < S; q0 += kBeginThreads) {
+        const int q = q0 + t;
+        long long want = 0, fan = 1, k = 0;
+        int sl = -1;
+        if (q < S) {
+            sl = (int)(((int64_t)q + waves) % S);
+            const int64_t held = rg.rem[sl];
+            if (held > 0) {
+                const bool root = held == 1 && (a.q.meta[rg.base[sl]] & kRootFlag) != 0;
+                fan = root ? 1 : (1ll << a.tb.sys[sl].n);
+                k = share / fan;
+                if (k < 1) k = 1;
+                if (k > held) k = held;
+                if (fan > 1) {
+                    // breadth while the region is less than half full, one parent at a time
+                    // (depth first) beyond: a region of R entries then still holds about
+                    // R / (2 fan) more levels of the depth-first walk
+                    const long long breadth = (rg.cap[sl] / 2 - held) / (fan - 1);
+                    if (k > breadth) k = breadth > 1 ? breadth : 1;
+                    if (held + k * (fan - 1) > rg.cap[sl]) k = 0;   // even one parent may not fit
+                }
+                want = k * fan;
+            }
+        }
+        // inclusive scan of the children wanted (Hillis-Steele over the block)
+        s_red[t] = want;
+        __syncthreads();
+        for (int off = 1; off < kBeginThreads; off <<= 1) {
+            const long long v = t >= off ? s_red[t - off] : 0;
+            __syncthreads();
+            s_red[t] += v;
+            __syncthreads();
+        }
+        const long long before = s_run + s_red[t] - want;
+        if (sl >= 0) {
+            long long give = k;
+            if (before + want > a.wave_children) {
+                const long long left = a.wave_children - before;
+                give = left > 0 ? left / fan : 0;
+            }
+            rg.prefix[sl] = give;   // parents popped; turned into a prefix below
+            if (rg.rem[sl] > 0 && give == 0 && s_active == 1) c->error = 1;   // cannot progress
+        }
+        __syncthreads();
+        if (t == kBeginThreads - 1) s_run += s_red[t];
+        __syncthreads();
+    }
+    // prefix over slots in slot order; rem = entries left below the popped parents
+    if (t == 0) {
+        long long run = 0, kids = 0;
+        for (int sl = 0; sl < S; sl++) {
+            const long long k = rg.prefix[sl];
+            rg.prefix[sl] = run;
+            run += k;
+            const bool root = rg.rem[sl] == 1 && (a.q.meta[rg.base[sl]] & kRootFlag) != 0;
+            kids += k * (root ? 1 : (1ll << a.tb.sys[sl].n));
+            rg.rem[sl] -= k;
+        }
+        rg.prefix[S] = run;
+        if (run == 0 && s_total > 0) c->error = 1;
+        c->top = s_total;
+        c->base = s_total - run;
+        c->k = run;
+        c->children = kids;
+        c->cursor = 0;
+        c->staged = 0;
+        for (int n = 0; n <= kMaxVars; n++) { c->surv_count[n] = 0; c->hs_cursor[n] = 0; }
+        c->cand_count = 0;
+        c->cand_cursor = 0;
+        c->waves += 1;
+    }
+}
+
+// queue index of the sweep's parent p
+__device__ __forceinline__ int64_t parent_index(const SweepArgs &a, int64_t base, int64_t p) {
+    if (a.rg.n == 0) return base + p;
+    int lo = 0, hi = a.rg.n;   // the slot s with prefix[s] <= p < prefix[s + 1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (a.rg.prefix[mid] <= p) lo = mid;
+        else hi = mid;
+    }
+    return a.rg.base[lo] + a.rg.rem[lo] + (p - a.rg.prefix[lo]);
+}
+
 __global__ void __launch_bounds__(kBeginThreads) k_wave_begin(SweepArgs a) {
     __shared__ long long s_sum[kBeginThreads];
     __shared__ long long s_first;
+    if (a.rg.n > 0) {
+        wave_begin_regions(a);
+        return;
+    }
     WaveCtl *c = a.ctl;
     const int64_t top = c->top;
     const int t = threadIdx.x;
@@ -133,7 +250,11 @@ __global__ void k_commit(SweepArgs a, int n_max) {
     const int64_t staged = c->staged, base = c->base;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < staged; i += stride) {
-        const int64_t d = base + i;
+        int64_t d = base + i;
+        if (a.rg.n > 0) {   // into the parent's own region, above what stays there
+            const int sl = a.stage.sys[i];
+            d = a.rg.base[sl] + a.rg.rem[sl] + (int64_t)atomicAdd(&a.rg.cursor[sl], 1ull);
+        }
         for (int j = 0; j < n_max; j++) {
             a.q.lo[j * a.q.cap + d] = a.stage.lo[j * a.stage.cap + i];
             a.q.mid[j * a.q.cap + d] = a.stage.mid[j * a.stage.cap + i];
@@ -180,7 +301,13 @@ __global__ void k_admit(SweepArgs a, const double *box_lo, const double *box_hi,
                         const int32_t *root_depth, int count, int n_max) {
     const int64_t top = a.ctl->top;
     for (int i = threadIdx.x; i < count; i += blockDim.x) {
-        const int64_t e = top + i;
+        int64_t e = top + i;
+        if (a.rg.n > 0) {   // the start of the system's own region
+            const int sl = slot[i];
+            e = a.rg.base[sl];
+            a.rg.rem[sl] = 1;
+            a.rg.cursor[sl] = 0;
+        }
         for (int j = 0; j < n_max; j++) {
             a.q.lo[j * a.q.cap + e] = box_lo[(size_t)i * n_max + j];
             a.q.mid[j * a.q.cap + e] = box_hi[(size_t)i * n_max + j];
@@ -194,97 +321,15 @@ __global__ void k_admit(SweepArgs a, const double *box_lo, const double *box_hi,
     if (threadIdx.x == 0) a.ctl->top = top + count;
 }
 
-// ---- purge: drop every queue entry of the cancelled systems ------------------------
-// Serving cancels a request whose time budget ran out; its entries may sit anywhere in
-// the queue.  Compaction without order: the kept entries above the new top move into
-// the holes below it (i-th hole <- i-th kept entry above).  Four launches between
-// sweeps: per-block kept counts, their prefix, hole positions, moves.
-constexpr int kPurgeBlocks = 1024, kPurgeThreads = 256;
-
-// exclusive prefix over the block of v; returns it and leaves the block total in *tot
-__device__ __forceinline__ long long block_excl_scan(long long v, long long *s_warp, long long *tot) {
-    const unsigned lane = lane_id();
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    long long x = v;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const long long y = __shfl_up_sync(kFull, x, off);
-        if ((int)lane >= off) x += y;
+// Serving with regions: a cancelled slot's region is emptied (its entries leave the total).
+__global__ void k_cancel_regions(SweepArgs a, const int32_t *cancel) {
+    for (int sl = threadIdx.x; sl < a.rg.n; sl += blockDim.x) {
+        if (!cancel[sl]) continue;
+        const int64_t held = a.rg.rem[sl] + (int64_t)a.rg.cursor[sl];
+        if (held) atomicAdd((unsigned long long *)&a.ctl->top, (unsigned long long)(-held));
+        a.rg.rem[sl] = 0;
+        a.rg.cursor[sl] = 0;
     }
-    if (lane == 31) s_warp[w] = x;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long run = 0;
-        for (int i = 0; i < nw; i++) { const long long t = s_warp[i]; s_warp[i] = run; run += t; }
-        s_warp[nw] = run;
-    }
-    __syncthreads();
-    const long long r = s_warp[w] + x - v;
-    *tot = s_warp[nw];
-    __syncthreads();
-    return r;
-}
-
-__device__ __forceinline__ bool purge_keep(const SweepArgs &a, const int32_t *cancel, int64_t e) {
-    return cancel[a.q.sys[e]] == 0;
-}
-
-__global__ void __launch_bounds__(kPurgeThreads) k_purge_count(SweepArgs a, const int32_t *cancel, int64_t top,
-                                                               int64_t per, long long *blk) {
-    __shared__ long long s_warp[kPurgeThreads / 32 + 1];
-    const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(b0 + per, top);
-    long long cnt = 0;
-    for (int64_t e = b0 + threadIdx.x; e < b1; e += blockDim.x) cnt += purge_keep(a, cancel, e) ? 1 : 0;
-    long long tot = 0;
-    block_excl_scan(cnt, s_warp, &tot);
-    if (threadIdx.x == 0) blk[blockIdx.x] = tot;
-}
-
-// blk[b] -> kept entries before block b; blk[kPurgeBlocks] = kept total = new top
-__global__ void __launch_bounds__(kPurgeBlocks) k_purge_scan(long long *blk) {
-    __shared__ long long s_warp[kPurgeBlocks / 32 + 1];
-    long long tot = 0;
-    const long long v = blk[threadIdx.x];
-    const long long r = block_excl_scan(v, s_warp, &tot);
-    blk[threadIdx.x] = r;
-    if (threadIdx.x == 0) blk[kPurgeBlocks] = tot;
-}
-
-// pass 0: every hole below the new top K records its position at its rank among those
-// holes, and the thread at K - 1 stores K0 = kept entries below K; pass 1: every kept
-// entry at or above K moves to the hole whose rank is its rank among those entries
-// (kb - K0, kb = kept entries before it); both sets have K - K0 members.  blk[kPurgeBlocks]
-// holds K, blk[kPurgeBlocks + 1] K0.
-__global__ void __launch_bounds__(kPurgeThreads) k_purge_move(SweepArgs a, const int32_t *cancel, int64_t top,
-                                                              int64_t per, long long *blk, uint32_t *hole,
-                                                              int pass, int n_max) {
-    __shared__ long long s_warp[kPurgeThreads / 32 + 1];
-    const long long K = blk[kPurgeBlocks];
-    const long long K0 = pass == 1 ? blk[kPurgeBlocks + 1] : 0;
-    const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(b0 + per, top);
-    long long before = blk[blockIdx.x];   // kept entries in [0, tile start)
-    for (int64_t t0 = b0; t0 < b1; t0 += blockDim.x) {
-        const int64_t e = t0 + threadIdx.x;
-        const bool in = e < b1;
-        const bool keep = in && purge_keep(a, cancel, e);
-        long long tot = 0;
-        const long long kb = before + block_excl_scan(keep ? 1 : 0, s_warp, &tot);   // kept in [0, e)
-        if (in && pass == 0) {
-            if (!keep && e < K) hole[e - kb] = (uint32_t)e;   // holes in [0, e) = e - kb
-            if (e == K - 1) blk[kPurgeBlocks + 1] = kb + (keep ? 1 : 0);
-        } else if (in && pass == 1 && keep && e >= K) {
-            const int64_t d = hole[kb - K0];
-            for (int j = 0; j < n_max; j++) {
-                a.q.lo[j * a.q.cap + d] = a.q.lo[j * a.q.cap + e];
-                a.q.mid[j * a.q.cap + d] = a.q.mid[j * a.q.cap + e];
-                a.q.hi[j * a.q.cap + d] = a.q.hi[j * a.q.cap + e];
-            }
-            a.q.sys[d] = a.q.sys[e];
-            a.q.meta[d] = a.q.meta[e];
-        }
-        before += tot;
-    }
-    if (pass == 1 && blockIdx.x == 0 && threadIdx.x == 0) a.ctl->top = K;
 }
 
 __global__ void k_loop_cond(SweepArgs a, cudaGraphConditionalHandle h) {
@@ -519,8 +564,8 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(SweepArgs a) {
     }
     if (block_mode) {
         for (int64_t p = blockIdx.x; p < K; p += gridDim.x)
-            eval_parent<true>(a, ctl, s_blob, s_tv_base, s_p[0], s_f[0], s_e[0], &s_flag, base + p, threadIdx.x,
-                              blockDim.x);
+            eval_parent<true>(a, ctl, s_blob, s_tv_base, s_p[0], s_f[0], s_e[0], &s_flag, parent_index(a, base, p),
+                              threadIdx.x, blockDim.x);
         return;
     }
     float4 *s_tv = s_tv_base + (size_t)w * a.tv_stride;
@@ -529,7 +574,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval(SweepArgs a) {
         if (lane == 0) p = atomicAdd(&ctl->cursor, 1);
         p = __shfl_sync(kFull, p, 0);
         if (p >= K) break;
-        eval_parent<false>(a, ctl, s_blob, s_tv, s_p[w], s_f[w], s_e[w], &s_flag, base + p, lane, 32u);
+        eval_parent<false>(a, ctl, s_blob, s_tv, s_p[w], s_f[w], s_e[w], &s_flag, parent_index(a, base, p), lane, 32u);
     }
 }
 
@@ -698,14 +743,8 @@ cudaError_t launch_admit(const SweepArgs &a, const double *d_lo, const double *d
     return cudaGetLastError();
 }
 
-cudaError_t launch_purge(const SweepArgs &a, const int32_t *d_cancel, int64_t top, int n_max, long long *d_blk,
-                         uint32_t *d_hole, cudaStream_t st) {
-    if (top <= 0) return cudaSuccess;
-    const int64_t per = (top + kPurgeBlocks - 1) / kPurgeBlocks;
-    k_purge_count<<<kPurgeBlocks, kPurgeThreads, 0, st>>>(a, d_cancel, top, per, d_blk);
-    k_purge_scan<<<1, kPurgeBlocks, 0, st>>>(d_blk);
-    k_purge_move<<<kPurgeBlocks, kPurgeThreads, 0, st>>>(a, d_cancel, top, per, d_blk, d_hole, 0, n_max);
-    k_purge_move<<<kPurgeBlocks, kPurgeThreads, 0, st>>>(a, d_cancel, top, per, d_blk, d_hole, 1, n_max);
+cudaError_t launch_cancel_regions(const SweepArgs &a, const int32_t *d_cancel, cudaStream_t st) {
+    k_cancel_regions<<<1, 1024, 0, st>>>(a, d_cancel);
     return cudaGetLastError();
 }
 

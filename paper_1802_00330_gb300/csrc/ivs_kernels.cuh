@@ -34,6 +34,7 @@ struct SweepArgs {
     int32_t blob_smem;           // bytes of that blob
     int32_t tv_stride;           // term-combination entries per warp region (0: no tables)
     int32_t eval_warps;          // warps per block of k_eval
+    DevRegions rg;               // serving: per-system queue regions (rg.n == 0: shared stack)
 };
 
 // dynamic shared memory of k_eval (blob cache + the warps' combination tables) and the
@@ -60,15 +61,20 @@ cudaError_t build_sweep_graph(const SweepArgs &a, const int *hs_dims, int n_hs_d
 cudaError_t run_probe(int kind, int num_sms, double *ops, float *ms);
 cudaError_t launch_seed_roots(const SweepArgs &a, const double *d_box_lo, const double *d_box_hi,
                               const int32_t *d_root_depth, int n_sys, int n_max, cudaStream_t st);
-// appends initial boxes of newly admitted systems (slot ids) on top of the queue
+// serving with regions: empties the regions of the slots with d_cancel[s] != 0 (between
+// sweeps) and lowers the queue total accordingly
+cudaError_t launch_cancel_regions(const SweepArgs &a, const int32_t *d_cancel, cudaStream_t st);
+// appends initial boxes of newly admitted systems (slot ids) on top of the queue, or at
+// the start of each system's region
 cudaError_t launch_admit(const SweepArgs &a, const double *d_lo, const double *d_hi, const int32_t *d_slot,
                          const int32_t *d_depth, int count, int n_max, cudaStream_t st);
-// Serving: removes every queue entry whose system has d_cancel[sys] != 0 (between
-// sweeps; `top` = the current queue size).  d_blk: kPurgeScratch long longs;
-// d_hole: `top` uint32 entries.  Sets ctl->top to the entries left.
-constexpr int kPurgeScratch = 1024 + 2;
-cudaError_t launch_purge(const SweepArgs &a, const int32_t *d_cancel, int64_t top, int n_max, long long *d_blk,
-                         uint32_t *d_hole, cudaStream_t st);
+// serving with regions: empties the regions of the slots with d_cancel[s] != 0 (between
+// sweeps) and lowers the queue total accordingly
+cudaError_t launch_cancel_regions(const SweepArgs &a, const int32_t *d_cancel, cudaStream_t st);
+// appends initial boxes of newly admitted systems (slot ids) on top of the queue, or at
+// the start of each system's region
+cudaError_t launch_admit(const SweepArgs &a, const double *d_lo, const double *d_hi, const int32_t *d_slot,
+                         const int32_t *d_depth, int count, int n_max, cudaStream_t st);
 // Hansen-Sengupta + accept/split kernel for dimension n (ivs_hs_*.cu)
 cudaError_t launch_hs_dim1(const SweepArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_hs_dim2(const SweepArgs &a, int num_sms, cudaStream_t st);

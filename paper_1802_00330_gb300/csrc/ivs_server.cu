@@ -14,6 +14,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -86,10 +87,11 @@ struct ivs_server {
     int32_t *h_rslot = nullptr, *h_rdepth = nullptr;
     double *d_rlo = nullptr, *d_rhi = nullptr;
     int32_t *d_rslot = nullptr, *d_rdepth = nullptr;
-    int32_t *d_cancel = nullptr;                   // per slot: 1 = its queue entries are purged
-    long long *d_pblk = nullptr;                   // purge scratch
-    uint32_t *d_hole = nullptr;                    // purge hole positions (queue capacity)
-    int64_t q_cap = 0, rps = 0, reserved = 0;
+    int32_t *d_cancel = nullptr;                   // per slot: 1 = its region is emptied
+    int64_t *h_region = nullptr;                   // pinned: a slot's region base and size
+    int64_t q_cap = 0, rps = 0;
+    std::map<int64_t, int64_t> free_regions;       // queue entries not held by a slot: start -> size
+    std::vector<std::pair<int64_t, int64_t>> region_of;   // per slot
     std::vector<Slot> slots;
     std::vector<int> free_slots;
     std::atomic<int> active{0};
@@ -109,6 +111,8 @@ struct ivs_server {
     void loop();
     int step(std::vector<std::pair<uint64_t, ivs_result *>> &finished);
     void fail_all_active(int status, std::vector<std::pair<uint64_t, ivs_result *>> &finished);
+    bool region_alloc(int64_t size, int64_t *start);
+    void region_free(int slot);
 };
 
 ivs_server::~ivs_server() {
@@ -124,7 +128,7 @@ ivs_server::~ivs_server() {
     if (graph) cudaGraphDestroy(graph);
     if (ws) cudaFree(ws);
     if (tables) cudaFree(tables);
-    if (d_hole) cudaFree(d_hole);
+    if (h_region) cudaFreeHost(h_region);
     if (h_ctl) cudaFreeHost(h_ctl);
     if (h_stats) cudaFreeHost(h_stats);
     if (h_limit) cudaFreeHost(h_limit);
@@ -170,20 +174,29 @@ int ivs_server::init() {
     const size_t sys_bytes = align_up((size_t)S * sizeof(DevSys), 256);
     const size_t blob_bytes = (size_t)S * kBlobSlot;
     const size_t adm_bytes = align_up((size_t)S * (2 * (size_t)n_max * sizeof(double) + 2 * sizeof(int32_t)), 256);
-    const size_t purge_bytes = (size_t)kPurgeScratch * sizeof(long long) + (size_t)S * sizeof(int32_t);
-    CUDA_TRY(cudaMalloc(&tables, sys_bytes + blob_bytes + adm_bytes + purge_bytes));
-    CUDA_TRY(cudaMemsetAsync(tables, 0, sys_bytes + blob_bytes + adm_bytes + purge_bytes, stream));
+    // per slot: cancel flag; the region arrays (base, cap, rem, prefix (S + 1), cursor)
+    const size_t slot_bytes = align_up((size_t)S * sizeof(int32_t), 256) + (size_t)(5 * S + 1) * sizeof(int64_t);
+    CUDA_TRY(cudaMalloc(&tables, sys_bytes + blob_bytes + adm_bytes + slot_bytes));
+    CUDA_TRY(cudaMemsetAsync(tables, 0, sys_bytes + blob_bytes + adm_bytes + slot_bytes, stream));
     d_sys = (DevSys *)tables;
     d_blobs = (char *)tables + sys_bytes;
     d_rlo = (double *)(d_blobs + blob_bytes);
     d_rhi = d_rlo + (size_t)S * n_max;
     d_rslot = (int32_t *)(d_rhi + (size_t)S * n_max);
     d_rdepth = d_rslot + S;
-    d_pblk = (long long *)(d_blobs + blob_bytes + adm_bytes);
-    d_cancel = (int32_t *)(d_pblk + kPurgeScratch);
+    d_cancel = (int32_t *)(d_blobs + blob_bytes + adm_bytes);
+    int64_t *rg_mem = (int64_t *)((char *)d_cancel + align_up((size_t)S * sizeof(int32_t), 256));
     if (q_cap > (int64_t)0xFFFFFFFFLL) return fail(IVS_ERR_INVALID, "server queue above 2^32 entries");
-    e = cudaMalloc(&d_hole, (size_t)q_cap * sizeof(uint32_t));
-    if (e != cudaSuccess) return fail(IVS_ERR_NOMEM, std::string("cudaMalloc purge buffer: ") + cudaGetErrorString(e));
+    // one queue region per slot, carved from the queue at admission
+    a.rg.base = rg_mem;
+    a.rg.cap = rg_mem + S;
+    a.rg.rem = rg_mem + 2 * S;
+    a.rg.cursor = (unsigned long long *)(rg_mem + 3 * S);
+    a.rg.prefix = rg_mem + 4 * S;
+    a.rg.n = S;
+    free_regions[0] = q_cap;
+    region_of.assign((size_t)S, {0, 0});
+    CUDA_TRY(cudaMallocHost((void **)&h_region, 2 * (size_t)S * sizeof(int64_t)));
     a.tb.sys = d_sys;
     a.tb.blobs = d_blobs;
     CUDA_TRY(cudaMallocHost((void **)&h_ctl, sizeof(WaveCtl)));
@@ -219,15 +232,49 @@ void ivs_server::fail_all_active(int status, std::vector<std::pair<uint64_t, ivs
         finished.push_back({slots[s].req.ticket, r});
         slots[s].used = false;
         free_slots.push_back(s);
-        reserved -= slots[s].req.reserve;
+        region_free(s);
     }
     active = 0;
+}
+
+// first fit over the free queue segments
+bool ivs_server::region_alloc(int64_t size, int64_t *start) {
+    for (auto it = free_regions.begin(); it != free_regions.end(); ++it) {
+        if (it->second < size) continue;
+        *start = it->first;
+        const int64_t rest = it->second - size;
+        const int64_t at = it->first + size;
+        free_regions.erase(it);
+        if (rest > 0) free_regions[at] = rest;
+        return true;
+    }
+    return false;
+}
+
+void ivs_server::region_free(int slot) {
+    auto &rg = region_of[(size_t)slot];
+    if (rg.second <= 0) return;
+    int64_t st = rg.first, sz = rg.second;
+    rg = {0, 0};
+    auto nx = free_regions.lower_bound(st);
+    if (nx != free_regions.end() && st + sz == nx->first) {   // merge with the next segment
+        sz += nx->second;
+        nx = free_regions.erase(nx);
+    }
+    if (nx != free_regions.begin()) {                        // and with the previous one
+        auto pv = std::prev(nx);
+        if (pv->first + pv->second == st) {
+            pv->second += sz;
+            return;
+        }
+    }
+    free_regions[st] = sz;
 }
 
 // One step: admit, run sweeps, collect finished systems.  Returns a CUDA status.
 int ivs_server::step(std::vector<std::pair<uint64_t, ivs_result *>> &finished) {
     // (1) requests past their time budget leave the queue at once: their entries are
-    // purged wherever they sit, and they complete in this step (IVS_ERR_TIMEOUT)
+    // dropped (their region is emptied), and they complete in this step (IVS_ERR_TIMEOUT)
     {
         const auto now0 = Clock::now();
         bool any = false;
@@ -240,21 +287,22 @@ int ivs_server::step(std::vector<std::pair<uint64_t, ivs_result *>> &finished) {
             CUDA_TRY(cudaMemsetAsync(d_cancel + s, 0x01, sizeof(int32_t), stream));
             CUDA_TRY(cudaMemsetAsync(a.stats + (size_t)s * ST_COUNT + ST_LIVE, 0, sizeof(unsigned long long), stream));
         }
-        if (any) CUDA_TRY(launch_purge(a, d_cancel, h_ctl->top, n_max, d_pblk, d_hole, stream));
+        if (any) CUDA_TRY(launch_cancel_regions(a, d_cancel, stream));
     }
     // (2) admission
     std::vector<Request> admit;
     std::vector<int> admit_slot;
     {
         std::lock_guard<std::mutex> lk(mu);
-        while (!waiting.empty() && !free_slots.empty() &&
-               (active.load() + (int)admit.size() == 0 || reserved + waiting.front().reserve <= q_cap / 2) &&
-               h_ctl->top + (int64_t)admit.size() + 1 <= q_cap) {
+        // admission by memory: a request waits until a slot and a queue region of its
+        // reservation are free (in arrival order)
+        int64_t start = 0;
+        while (!waiting.empty() && !free_slots.empty() && region_alloc(waiting.front().reserve, &start)) {
             admit.push_back(std::move(waiting.front()));
             waiting.pop_front();
             admit_slot.push_back(free_slots.back());
             free_slots.pop_back();
-            reserved += admit.back().reserve;
+            region_of[(size_t)admit_slot.back()] = {start, admit.back().reserve};
         }
     }
     int n_adm = 0;
@@ -270,7 +318,7 @@ int ivs_server::step(std::vector<std::pair<uint64_t, ivs_result *>> &finished) {
             if (r) { r->status = IVS_ERR_INVALID; r->n = rq.n; }
             finished.push_back({rq.ticket, r});
             free_slots.push_back(s);
-            reserved -= rq.reserve;
+            region_free(s);
             continue;
         }
         d.shadow = (rq.opt.prefilter_fp32 && shadow_safe(&sv, rq.lo.data(), rq.hi.data())) ? 1 : 0;
@@ -281,6 +329,10 @@ int ivs_server::step(std::vector<std::pair<uint64_t, ivs_result *>> &finished) {
         CUDA_TRY(cudaMemcpyAsync(d_blobs + d.blob_off, h.blobs.data(), h.blobs.size(), cudaMemcpyHostToDevice, stream));
         CUDA_TRY(cudaMemsetAsync(a.stats + (size_t)s * ST_COUNT, 0, ST_COUNT * sizeof(unsigned long long), stream));
         CUDA_TRY(cudaMemsetAsync(d_cancel + s, 0, sizeof(int32_t), stream));
+        h_region[2 * s] = region_of[(size_t)s].first;
+        h_region[2 * s + 1] = region_of[(size_t)s].second;
+        CUDA_TRY(cudaMemcpyAsync(a.rg.base + s, &h_region[2 * s], sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+        CUDA_TRY(cudaMemcpyAsync(a.rg.cap + s, &h_region[2 * s + 1], sizeof(int64_t), cudaMemcpyHostToDevice, stream));
         for (int j = 0; j < n_max; j++) {
             h_rlo[(size_t)n_adm * n_max + j] = j < rq.n ? rq.lo[j] : 0.0;
             h_rhi[(size_t)n_adm * n_max + j] = j < rq.n ? rq.hi[j] : 0.0;
@@ -323,6 +375,8 @@ int ivs_server::step(std::vector<std::pair<uint64_t, ivs_result *>> &finished) {
         // the queue overflowed despite the reservations: fail the systems in flight, restart empty
         fail_all_active(IVS_ERR_NOMEM, finished);
         CUDA_TRY(launch_seed_roots(a, d_rlo, d_rhi, d_rdepth, 0, n_max, stream));
+        CUDA_TRY(cudaMemsetAsync(a.rg.rem, 0, slots.size() * sizeof(int64_t), stream));
+        CUDA_TRY(cudaMemsetAsync(a.rg.cursor, 0, slots.size() * sizeof(unsigned long long), stream));
         CUDA_TRY(cudaMemcpyAsync(h_ctl, a.ctl, sizeof(WaveCtl), cudaMemcpyDeviceToHost, stream));
         CUDA_TRY(cudaStreamSynchronize(stream));
         return IVS_OK;
@@ -380,7 +434,7 @@ int ivs_server::step(std::vector<std::pair<uint64_t, ivs_result *>> &finished) {
         finished.push_back({rq.ticket, r});
         slots[s].used = false;
         free_slots.push_back(s);
-        reserved -= rq.reserve;
+        region_free(s);
         active--;
     }
     return IVS_OK;
@@ -483,7 +537,8 @@ int ivs_server_submit(ivs_server *sv, const ivs_system *s, const double *box_lo,
     rq.lo.assign(box_lo, box_lo + s->n_vars);
     rq.hi.assign(box_hi, box_hi + s->n_vars);
     rq.opt = *opt;
-    rq.reserve = (int64_t)(64.0 * sv->cfg.reserve_factor * (double)((int64_t)1 << s->n_vars));
+    rq.reserve = std::max<int64_t>((int64_t)(64.0 * sv->cfg.reserve_factor * (double)((int64_t)1 << s->n_vars)),
+                                   ((int64_t)1 << s->n_vars) + 1);
     rq.t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(sv->mu);

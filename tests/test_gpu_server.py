@@ -145,3 +145,37 @@ def test_time_budget_frees_the_queue(B):
         assert same(again, res[0])
     finally:
         sv.close()
+
+
+def test_each_request_gets_its_share(B):
+    """Every request in flight has its own queue region and a fair share of each sweep:
+    small requests interleaved with hard ones in one burst finish promptly and exactly
+    while the hard ones run until their time budget."""
+    hard = [synth.config_n10()] * 3
+    small = synth.config_batched(count=12, seed=1212, n_range=(2, 4))
+    sv = B.Server(workspace_bytes=1 << 31, max_slots=32, wave_children=1 << 20, max_vars=10)
+    try:
+        tickets, kinds = [], []
+        for k, s in enumerate(small):
+            if k % 4 == 0 and k // 4 < len(hard):
+                tickets.append(sv.submit(hard[k // 4], time_budget_s=6.0))
+                kinds.append("hard")
+            tickets.append(sv.submit(s))
+            kinds.append(k)
+        t0 = time.time()
+        done_small = {}
+        for t, kind in zip(tickets, kinds):
+            if kind == "hard":
+                continue
+            r = wait_all(sv, [t], budget_s=60.0)[0]
+            done_small[kind] = (time.time() - t0, r)
+        # all small requests finish well before the hard ones' budget runs out
+        assert max(v[0] for v in done_small.values()) < 3.0, [round(v[0], 2) for v in done_small.values()]
+        for k, (_, r) in done_small.items():
+            assert same(r, B.solve(small[k])), k
+        for t, kind in zip(tickets, kinds):
+            if kind == "hard":
+                assert wait_all(sv, [t], budget_s=60.0)[0]["status"] == 4
+        assert sv.stats()["last_error"] == ""
+    finally:
+        sv.close()
