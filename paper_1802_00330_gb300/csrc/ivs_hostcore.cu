@@ -91,7 +91,22 @@ void pack_blob(HostTables &h, const SysBuild &b, DevSys &d, int n_fterms) {
         tv_off.push_back(tv_off.back() + (1 << nf));
     }
     const int TF = tv_ok ? n_fterms : 0, E = tv_ok ? (int)tv_map.size() : 0;
-    const BlobLayout L = blob_layout(T, P, F, TF, E);
+    // child-index table: for each F term and each child c (n bits), its table entry
+    // tv_off[t] + (c's bits in the term's variables); kept small (n <= 8, <= 16384 entries)
+    std::vector<uint16_t> cix;
+    if (TF > 0 && d.n <= 8 && (int64_t)TF << d.n <= 16384) {
+        cix.resize((size_t)TF << d.n);
+        for (int t = 0; t < TF; t++) {
+            const int nf = term_nf(b.tinfo[t]), f0 = term_f0(b.tinfo[t]);
+            for (int c = 0; c < (1 << d.n); c++) {
+                unsigned q = 0;
+                for (int f = 0; f < nf; f++) q |= ((unsigned)(c >> (b.fac[f0 + f] >> 4)) & 1u) << f;
+                cix[((size_t)t << d.n) + c] = (uint16_t)(tv_off[t] + (int)q);
+            }
+        }
+    }
+    const int CX = (int)cix.size();
+    const BlobLayout L = blob_layout(T, P, F, TF, E, CX);
     const size_t off = h.blobs.size();
     h.blobs.resize(off + L.bytes, 0);
     char *base = h.blobs.data() + off;
@@ -113,6 +128,7 @@ void pack_blob(HostTables &h, const SysBuild &b, DevSys &d, int n_fterms) {
         std::memcpy(base + L.tv_off, tv_off.data(), 4u * (TF + 1));
         std::memcpy(base + L.tv_map, tv_map.data(), 4u * E);
     }
+    if (CX) std::memcpy(base + L.cix, cix.data(), 2u * CX);
     if (F) std::memcpy(base + L.fac, b.fac.data(), (size_t)F);
     d.blob_off = (int64_t)off;
     d.n_terms = T;
@@ -120,6 +136,7 @@ void pack_blob(HostTables &h, const SysBuild &b, DevSys &d, int n_fterms) {
     d.n_facs = F;
     d.n_fterms = TF;
     d.n_tv = E;
+    d.n_cix = CX;
     d.blob_bytes = (int32_t)L.bytes;
 }
 

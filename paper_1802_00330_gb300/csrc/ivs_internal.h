@@ -56,6 +56,7 @@ struct DevSys {
     int32_t n_fterms;      // terms of the equations F_i
     int32_t n_tv;          // term-combination entries (0: no per-parent table)
     int32_t centred;       // 1: centred-form exclusion test before Hansen-Sengupta
+    int32_t n_cix;         // child-index entries (n_fterms << n; 0: none)
 };
 
 struct DevTables {

@@ -19,11 +19,11 @@
 namespace ivs {
 
 // byte layout of a system blob with T terms, P polynomials, F factors, TF terms in the
-// equations F_i and E term-combination entries
+// equations F_i, E term-combination entries and CX child-index entries
 struct BlobLayout {
-    uint32_t cs, clo, chi, clo32, chi32, poly_off, tinfo, tv_off, tv_map, fac, bytes;
+    uint32_t cs, clo, chi, clo32, chi32, poly_off, tinfo, tv_off, tv_map, cix, fac, bytes;
 };
-__host__ __device__ inline BlobLayout blob_layout(int T, int P, int F, int TF = 0, int E = 0) {
+__host__ __device__ inline BlobLayout blob_layout(int T, int P, int F, int TF = 0, int E = 0, int CX = 0) {
     BlobLayout L;
     uint32_t o = 0;
     L.cs = o;        o += 16u * T;
@@ -35,6 +35,7 @@ __host__ __device__ inline BlobLayout blob_layout(int T, int P, int F, int TF = 
     L.tinfo = o;     o += 4u * T;
     L.tv_off = o;    o += 4u * (TF + 1);
     L.tv_map = o;    o += 4u * E;
+    L.cix = o;       o += (2u * CX + 3u) & ~3u;
     L.fac = o;       o += (uint32_t)F;
     L.bytes = (o + 15u) & ~15u;
     return L;
@@ -55,11 +56,12 @@ struct SysTab {
     const uint32_t *tinfo;   // term info words (above)
     const int32_t *tv_off;   // [TF + 1]: first combination entry of each F term
     const uint32_t *tv_map;  // [E]: term << 8 | combination of its variables' halves
+    const uint16_t *cix;     // [TF << n] (if present): entry of F term t for child c at (t << n) + c
     const uint8_t *fac;
 };
 
 __device__ __forceinline__ SysTab make_tab(const char *blob, const DevSys &S) {
-    const BlobLayout L = blob_layout(S.n_terms, S.n_polys, S.n_facs, S.n_fterms, S.n_tv);
+    const BlobLayout L = blob_layout(S.n_terms, S.n_polys, S.n_facs, S.n_fterms, S.n_tv, S.n_cix);
     SysTab t;
     t.cs = reinterpret_cast<const float4 *>(blob + L.cs);
     t.clo = reinterpret_cast<const double *>(blob + L.clo);
@@ -70,6 +72,7 @@ __device__ __forceinline__ SysTab make_tab(const char *blob, const DevSys &S) {
     t.tinfo = reinterpret_cast<const uint32_t *>(blob + L.tinfo);
     t.tv_off = reinterpret_cast<const int32_t *>(blob + L.tv_off);
     t.tv_map = reinterpret_cast<const uint32_t *>(blob + L.tv_map);
+    t.cix = reinterpret_cast<const uint16_t *>(blob + L.cix);
     t.fac = reinterpret_cast<const uint8_t *>(blob + L.fac);
     return t;
 }
@@ -220,18 +223,26 @@ __device__ __forceinline__ float4 term_shadow(const SysTab &T, int t, const Coor
 }
 
 // FP32 shadow decision of child c from its parent's table tv (same result as
-// decide_shadow on the child): 0 exclude, 1 keep, 2 undecided
+// decide_shadow on the child): 0 exclude, 1 keep, 2 undecided.  The entry of a term for
+// the child is read from the child-index table when the blob has one (small n), else
+// gathered from the child's bits in the term's variables.
 __device__ __forceinline__ int decide_from_table(const SysTab &T, const DevSys &S, const float4 *tv, unsigned c) {
     bool undecided = false;
     for (int i = 0; i < S.m; i++) {
         const int t0 = T.poly_off[S.f_poly + i], t1 = T.poly_off[S.f_poly + i + 1];
         shv acc = {0.f, 0.f, 0.f, 0.f};
         for (int t = t0; t < t1; t++) {
-            const uint32_t info = T.tinfo[t];
-            const int nf = term_nf(info), f0 = term_f0(info);
-            unsigned q = 0;
-            for (int f = 0; f < nf; f++) q |= ((c >> (T.fac[f0 + f] >> 4)) & 1u) << f;
-            const float4 v = tv[T.tv_off[t] + (int)q];
+            int e;
+            if (S.n_cix > 0) {
+                e = T.cix[((unsigned)t << S.n) + c];
+            } else {
+                const uint32_t info = T.tinfo[t];
+                const int nf = term_nf(info), f0 = term_f0(info);
+                unsigned q = 0;
+                for (int f = 0; f < nf; f++) q |= ((c >> (T.fac[f0 + f] >> 4)) & 1u) << f;
+                e = T.tv_off[t] + (int)q;
+            }
+            const float4 v = tv[e];
             const shv sv = {v.x, v.y, v.z, v.w};
             acc = (t == t0) ? sv : sh_add(acc, sv);
         }
