@@ -87,11 +87,12 @@ def hs_ops(s):
 
 
 # ---- measured DRAM traffic of the dominant kernel ----------------------------------------
-# ncu's dram__bytes_read.sum + dram__bytes_write.sum per k_hs<6> launch, averaged over the
-# 10 launches of one n=6 solve (profiles/k_hs_n6_dram.md).  Valid only for the kernel sources
+# ncu's dram__bytes_read.sum + dram__bytes_write.sum of the Hansen-Sengupta stage per sweep
+# (k_hs<6> and k_hs_coop<6>), averaged over the 10 sweeps of one n=6 solve (an ncu
+# capture of this workload).  Valid only for the kernel sources
 # it was taken with: the bench reports null once their hash differs.
-HS_TRAFFIC_N6 = {"sources_sha256": "efce3556e0e440406850e8517e608dcb96b33e52ba8cac90000dd724964e0e4e",
-                 "bytes_per_launch": 414720}
+HS_TRAFFIC_N6 = {"sources_sha256": "46e29212266a09a7aabc9098d454daf8aca4c72431206ce84fe8f595376f3fbf",
+                 "bytes_per_launch": 474624}
 HS_SOURCES = ("ivs_hs.cuh", "ivs_tab.cuh", "ivs_interval.cuh", "ivs_internal.h", "ivs_kernels.cuh")
 
 
