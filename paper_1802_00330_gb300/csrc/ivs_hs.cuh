@@ -741,11 +741,13 @@ constexpr size_t kHsSmemLimit = 227 * 1024 - 64;
 // a cooperative CTA asks for at least this much, so no two share an SM
 constexpr size_t kOneCtaPerSm = 120 * 1024;
 
+// resident clusters of the cooperative kernel for a shared memory size, queried once per
+// size (the launchers may run on several host threads)
+int coop_clusters_cached(const void *func, int num_sms, int threads, size_t smem, cudaError_t *err);
+
 template <int N>
 static cudaError_t launch_hs_n(const SweepArgs &a, int num_sms, cudaStream_t st) {
     using C = hsd::Cfg<N>;
-    static int per_sm = 0;             // blocks per SM, found once per configuration
-    static size_t configured_smem = 0, configured_coop = 0;
     // cache the term table in shared memory when the plan holds one system and it fits
     const bool cache = a.single && (size_t)a.blob_smem + C::BYTES <= kHsSmemLimit;
     const size_t smem = (cache ? (size_t)a.blob_smem : 0) + C::BYTES;
@@ -754,38 +756,25 @@ static cudaError_t launch_hs_n(const SweepArgs &a, int num_sms, cudaStream_t st)
       if (num_sms >= 2 * hsd::kCS) {
         // narrow sweeps: clusters of kCS CTAs, one per SM, one chunk per cluster that can
         // be resident at once (a wider sweep runs faster in the independent form)
-        static int active_clusters = 0;
         const size_t csmem = smem > kOneCtaPerSm ? smem : kOneCtaPerSm;
-        if (configured_coop != csmem) {
-            cudaError_t e = cudaFuncSetAttribute(k_hs_coop<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
-            if (e != cudaSuccess) return e;
-            cudaLaunchConfig_t lc = {};
-            lc.gridDim = dim3((unsigned)((num_sms / hsd::kCS) * hsd::kCS));
-            lc.blockDim = dim3((unsigned)C::NT);
-            lc.dynamicSmemBytes = csmem;
-            int nc = 0;
-            e = cudaOccupancyMaxActiveClusters(&nc, k_hs_coop<N>, &lc);
-            if (e != cudaSuccess) return e;
-            active_clusters = nc;
-            configured_coop = csmem;
-        }
+        cudaError_t e = allow_max_dynamic_smem((const void *)k_hs_coop<N>);
+        if (e != cudaSuccess) return e;
+        const int active_clusters = coop_clusters_cached((const void *)k_hs_coop<N>, num_sms, C::NT, csmem, &e);
+        if (e != cudaSuccess) return e;
         if (active_clusters > 0) {
             coop_max = (long long)active_clusters * C::BB;
             k_hs_coop<N><<<active_clusters * hsd::kCS, C::NT, csmem, st>>>(a, cache ? 1 : 0, coop_max);
-            cudaError_t e = cudaGetLastError();
+            e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }
       }
     }
-    if (per_sm == 0 || configured_smem != smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_hs<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int bl = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, k_hs<N>, C::NT, smem);
-        if (e != cudaSuccess) return e;
-        per_sm = bl < 1 ? 1 : bl;
-        configured_smem = smem;
-    }
+    cudaError_t e = allow_max_dynamic_smem((const void *)k_hs<N>);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;   // blocks per SM at this shared memory size
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hs<N>, C::NT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
     k_hs<N><<<num_sms * per_sm, C::NT, smem, st>>>(a, cache ? 1 : 0, coop_max);
     return cudaGetLastError();
 }

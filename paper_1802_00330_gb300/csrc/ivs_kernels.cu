@@ -8,6 +8,10 @@
 // roundings), so the sorted result set is identical to the serial solver's.
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "ivs_internal.h"
 #include "ivs_interval.cuh"
 #include "ivs_kernels.cuh"
@@ -667,15 +671,49 @@ static cudaError_t launch_hs(const SweepArgs &a, int n, int num_sms, cudaStream_
     }
 }
 
+int coop_clusters_cached(const void *func, int num_sms, int threads, size_t smem, cudaError_t *err) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, int, size_t, int>, int> known;
+    int dev = 0;
+    *err = cudaGetDevice(&dev);
+    if (*err != cudaSuccess) return 0;
+    const auto key = std::make_tuple(func, num_sms, threads, smem, dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = known.find(key);
+    if (it != known.end()) return it->second;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)((num_sms / 4) * 4));
+    lc.blockDim = dim3((unsigned)threads);
+    lc.dynamicSmemBytes = smem;
+    int nc = 0;
+    *err = cudaOccupancyMaxActiveClusters(&nc, func, &lc);
+    if (*err != cudaSuccess) return 0;
+    known[key] = nc;
+    return nc;
+}
+
 size_t eval_smem_bytes(const SweepArgs &a) {
     return (size_t)(a.single ? a.blob_smem : 0) + (size_t)a.eval_warps * a.tv_stride * sizeof(float4);
 }
 
-cudaError_t configure_eval_kernels(const SweepArgs &a) {
-    cudaError_t e = cudaFuncSetAttribute(k_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)eval_smem_bytes(a));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_eval64, cudaFuncAttributeMaxDynamicSharedMemorySize, a.single ? a.blob_smem : 0);
+cudaError_t allow_max_dynamic_smem(const void *func) {
+    // The attribute is global to the kernel: every plan and server sets the same maximum,
+    // so one whose launches need less never lowers it under another's captured graph.
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
     return e;
+}
+
+cudaError_t configure_eval_kernels(const SweepArgs &a) {
+    (void)a;
+    cudaError_t e = allow_max_dynamic_smem((const void *)k_eval);
+    if (e != cudaSuccess) return e;
+    return allow_max_dynamic_smem((const void *)k_eval64);
 }
 
 cudaError_t launch_sweep(const SweepArgs &a, const int *hs_dims, int n_hs_dims, int eval_blocks,

@@ -41,6 +41,8 @@ struct SweepArgs {
 // kernels' limits; tv_stride / eval_warps come from choose_eval_layout
 size_t eval_smem_bytes(const SweepArgs &a);
 cudaError_t configure_eval_kernels(const SweepArgs &a);
+// raises a kernel's dynamic shared memory limit to the device maximum (idempotent)
+cudaError_t allow_max_dynamic_smem(const void *func);
 // picks eval_warps and tv_stride for the largest table `max_tv` of the plan's systems
 inline void choose_eval_layout(SweepArgs &a, int max_tv) {
     const size_t budget = 200 * 1024 - (size_t)(a.single ? a.blob_smem : 0);

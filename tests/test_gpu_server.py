@@ -179,3 +179,24 @@ def test_each_request_gets_its_share(B):
         assert sv.stats()["last_error"] == ""
     finally:
         sv.close()
+
+
+def test_plans_on_another_thread_while_serving(B):
+    """A server's captured sweep graph keeps working while other host threads build and run
+    plans of other shapes (the kernels' shared-memory limits are raised once, never
+    lowered)."""
+    small = synth.config_batched(count=6, seed=6060, n_range=(2, 4))
+    sv = B.Server(workspace_bytes=1 << 30, max_slots=64, wave_children=1 << 20, max_vars=10)
+    try:
+        th = sv.submit(synth.config_n10(), time_budget_s=2.0)
+        for s in small:                      # plans on this thread meanwhile
+            assert B.solve(s)["status"] == 0
+        assert B.solve(synth.config_n6())["status"] == 0
+        later = [sv.submit(s) for s in small]
+        res = wait_all(sv, later)
+        for s, r in zip(small, res):
+            assert same(r, B.solve(s))
+        assert wait_all(sv, [th])[0]["status"] == 4
+        assert sv.stats()["last_error"] == ""
+    finally:
+        sv.close()
