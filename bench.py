@@ -42,7 +42,19 @@ def workload(name):
     if name == "batched":
         return synth.config_batched(), ("batched: 4096 seeded systems, n~U{2..8}, 4-10 monomials/eq, deg<=3, "
                                          "int coef [-5,5], planted roots, box [-4,4]^n, tol 1e-6")
+    if name == "paper":
+        import dataclasses
+        here = os.path.dirname(os.path.abspath(__file__))
+        systems = [dataclasses.replace(synth.load_fixture(os.path.join(here, "tests", "golden", f"{k}.txt")), tol=1e-3)
+                   for k, _ in PAPER_SYSTEMS]
+        return systems, ("the paper's printed systems noon9 (box [-8,8]^9) and kinema (box [-32,32]^9), "
+                         "HS from the first round, tol 1e-3, one plan")
     raise SystemExit(f"unknown workload {name}")
+
+
+# the paper's printed systems with the width (grid level of the initial box) at which it
+# reports their isolated real roots (Section 4: noon9 19 at 0.0625, kinema 8 at 0.03125)
+PAPER_SYSTEMS = (("noon9", 8), ("kinema", 11))
 
 
 # ---- algorithmic work per box (FP64 operations the method needs) --------------------
@@ -91,8 +103,8 @@ def hs_ops(s):
 # (k_hs<6> and k_hs_coop<6>), averaged over the 10 sweeps of one n=6 solve (an ncu
 # capture of this workload).  Valid only for the kernel sources
 # it was taken with: the bench reports null once their hash differs.
-HS_TRAFFIC_N6 = {"sources_sha256": "46e29212266a09a7aabc9098d454daf8aca4c72431206ce84fe8f595376f3fbf",
-                 "bytes_per_launch": 474624}
+HS_TRAFFIC_N6 = {"sources_sha256": "fe4000215c5470c865ce2e3b1619a33ddf56076ed61706b844b9496c378d2a3b",
+                 "bytes_per_launch": 477952}
 HS_SOURCES = ("ivs_hs.cuh", "ivs_tab.cuh", "ivs_interval.cuh", "ivs_internal.h", "ivs_kernels.cuh")
 
 
@@ -287,6 +299,14 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
     # parity guard: the timed solve's result equals the warm-up solve's
     res = plan.result(0)
     assert np.array_equal(res["lo"], ref["lo"]) and np.array_equal(res["hi"], ref["hi"])
+    roots = None
+    if args.workload == "paper":
+        # Algorithm 5 backtracking to the paper's widths, then merged: isolated real roots
+        roots = {}
+        for k, (name, level) in enumerate(PAPER_SYSTEMS):
+            rk = plan.result(k)
+            s = systems[k]
+            roots[name] = B.backtrack(rk["lo"], rk["hi"], s.box_lo, s.box_hi, level, groups=True)[1]
 
     # plain FP64 path (prefilter off) on the same workload, same GPU
     plan64 = B.Plan(systems, opts={**base_opts, "prefilter_fp32": 0}, stream=stream,
@@ -314,8 +334,8 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
     s0 = systems[0]
     e2e_t = []
     e2e_boxes = 0
-    h2d = (s0.eq_offsets.nbytes + s0.coef_lo.nbytes + s0.coef_hi.nbytes + s0.exps.nbytes
-           + s0.box_lo.nbytes + s0.box_hi.nbytes)
+    h2d = sum(s.eq_offsets.nbytes + s.coef_lo.nbytes + s.coef_hi.nbytes + s.exps.nbytes + s.box_lo.nbytes
+              + s.box_hi.nbytes for s in systems)
     d2h = 0
     if len(systems) == 1:
         for _ in range(args.steps):
@@ -330,6 +350,7 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
             outs = B.solve_batch(systems, **base_opts)
             e2e_t.append(time.perf_counter() - t0)
             e2e_boxes += sum(o["stats"]["boxes"] for o in outs)
+            d2h = sum(o["lo"].nbytes + o["hi"].nbytes + o["flags"].nbytes + o["depth"].nbytes for o in outs)
     e2e = {"value": e2e_boxes / float(np.sum(e2e_t)), "unit": "boxes/s", "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h)}
 
@@ -410,6 +431,7 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
             "e2e": e2e,
             "gpu_launches": int(launches),
             "roofline": roofline, "prefilter_roofline": prefilter_roofline,
+            **({"isolated_roots": roots, "isolated_roots_paper": {"noon9": 19, "kinema": 8}} if roots else {}),
             "measured_rates": {"fp64_directed_ops_per_s": fp64_rate, "fp32_directed_ops_per_s": fp32_rate},
             "kernel_ms": {k: round(v[1], 4) for k, v in ktimes.items()},
             "host_loop_ms_per_step": 1e3 * float(np.mean(prof_t)),

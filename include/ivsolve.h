@@ -70,7 +70,9 @@ typedef struct ivs_options {
     double tol;              /* accept width (>= 0)                                   */
     int32_t hs_enable;       /* 1: Hansen-Sengupta sweep on boxes that survive F(X)    */
     int32_t hs_min_depth;    /* sweep only at depth >= this (the paper starts late)    */
-    int32_t hs_iters;        /* sweeps per visit (>= 1)                                */
+    int32_t hs_iters;        /* at most this many sweeps per visit (>= 1); they stop at
+                                the first sweep that leaves the box unchanged (Section
+                                2.3: iterated until the contraction stalls)             */
     int32_t prefilter_fp32;  /* 1: FP32 stage before FP64.  It carries float enclosures
                                 of both ends of every FP64 intermediate, so it drops a
                                 box only when FP64 would and keeps one only when FP64

@@ -546,6 +546,9 @@ int orc_solve(const orc_system *s, const double *box_lo, const double *box_hi,
                     if (Xn[j].lo != X[j].lo || Xn[j].hi != X[j].hi) changed = 1;
                 if (changed) res->st.hs_contracted++;
                 memcpy(X, Xn, sizeof(ivl) * (size_t)n);
+                /* iterated until the contraction stalls (Section 2.3): a sweep that leaves
+                 * the box unchanged would leave it unchanged again */
+                if (!changed) break;
             }
             if (dropped) { res->st.hs_empty++; continue; }
         }

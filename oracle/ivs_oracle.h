@@ -33,7 +33,8 @@ typedef struct {
     double tol;             /* accept when max_j RN(hi_j - lo_j) <= tol            */
     int32_t hs_enable;      /* 1: Hansen-Sengupta step on every kept box            */
     int32_t hs_min_depth;   /* HS only at depth >= hs_min_depth                     */
-    int32_t hs_iters;       /* Gauss-Seidel sweeps per visit (>= 1)                 */
+    int32_t hs_iters;       /* at most this many Gauss-Seidel sweeps per visit (>= 1);
+                               they stop at the first sweep that changes nothing       */
     int32_t root_depth;     /* depth given to the initial box                       */
     int32_t max_depth;      /* a box that would split past it is returned flagged   */
     int32_t order;          /* 0 LIFO, 1 FIFO, 2 seeded random pop                  */

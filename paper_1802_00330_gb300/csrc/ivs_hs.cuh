@@ -596,6 +596,9 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
                         sd[C::XC + j * BB + b] = midpoint_rn(ylo, yhi);
                     }
                     st_con += changed ? 1u : 0u;
+                    // iterated until the contraction stalls (Section 2.3): a sweep that
+                    // leaves the box unchanged would leave it unchanged again
+                    if (!changed) stopped = true;
                 }
             }
             __syncthreads();

@@ -133,6 +133,13 @@ def test_edge_cases(gpu, orc):
     assert_same(gpu.solve(s), orc.solve(s))
 
 
+def test_iterated_sweeps_until_stall(gpu, orc):
+    """Up to 6 sweeps per visit, stopping at the first that changes nothing: same boxes and
+    counters as the oracle."""
+    for s in synth.config_batched(count=8, seed=4646, n_range=(2, 5)):
+        assert_same(gpu.solve(s, hs_iters=6, tol=1e-4), orc.solve(s, hs_iters=6, tol=1e-4))
+
+
 def test_budget_flags(gpu):
     s = synth.config_n6()
     g = gpu.solve(s, max_boxes=5000)

@@ -256,3 +256,21 @@ def test_hs_drops_root_free_box(orc):
     s = synth.parse_system(["x1^2 - 2"], 1)
     rc, _, _ = orc.hs_step(s, [2.0], [3.0])
     assert rc == 1
+
+
+def test_hs_sweep_that_changes_nothing_changes_nothing_again(orc):
+    """The premise of stopping a visit's sweeps at the first sweep that leaves the box
+    unchanged: the sweep is a function of the box, so the next one is identical."""
+    rng = random.Random(77)
+    for s in (synth.config_n2(), synth.config_n6()):
+        for _ in range(20):
+            lo, hi = _rand_box(rng, s.n_vars, float(s.box_lo[0]), float(s.box_hi[0]))
+            for _ in range(12):
+                rc, nlo, nhi = orc.hs_step(s, lo, hi)
+                if rc != 0:
+                    break
+                if np.array_equal(nlo, lo) and np.array_equal(nhi, hi):
+                    rc2, nlo2, nhi2 = orc.hs_step(s, nlo, nhi)
+                    assert rc2 == 0 and np.array_equal(nlo2, nlo) and np.array_equal(nhi2, nhi)
+                    break
+                lo, hi = nlo, nhi
