@@ -42,3 +42,13 @@ def test_reduce_over_two_gloo_ranks():
         assert p.exitcode == 0
     for rank, t, b in out:
         assert t == 2.5 and b == 3000.0
+
+
+def test_oracle_all_cores_baseline_counts_boxes():
+    """The all-cores oracle baseline runs independent spawned processes over the top-level
+    sub-boxes and counts what they processed."""
+    import bench
+    from paper_1802_00330_gb300 import synth
+    s = synth.config_n2()
+    boxes, secs, cores = bench.oracle_all_cores(s, 2000, cores=2)
+    assert cores == 2 and secs > 0 and 0 < boxes <= 2 * 2000
