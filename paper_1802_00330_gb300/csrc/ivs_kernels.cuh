@@ -70,13 +70,6 @@ cudaError_t launch_cancel_regions(const SweepArgs &a, const int32_t *d_cancel, c
 // the start of each system's region
 cudaError_t launch_admit(const SweepArgs &a, const double *d_lo, const double *d_hi, const int32_t *d_slot,
                          const int32_t *d_depth, int count, int n_max, cudaStream_t st);
-// serving with regions: empties the regions of the slots with d_cancel[s] != 0 (between
-// sweeps) and lowers the queue total accordingly
-cudaError_t launch_cancel_regions(const SweepArgs &a, const int32_t *d_cancel, cudaStream_t st);
-// appends initial boxes of newly admitted systems (slot ids) on top of the queue, or at
-// the start of each system's region
-cudaError_t launch_admit(const SweepArgs &a, const double *d_lo, const double *d_hi, const int32_t *d_slot,
-                         const int32_t *d_depth, int count, int n_max, cudaStream_t st);
 // Hansen-Sengupta + accept/split kernel for dimension n (ivs_hs_*.cu)
 cudaError_t launch_hs_dim1(const SweepArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_hs_dim2(const SweepArgs &a, int num_sms, cudaStream_t st);
