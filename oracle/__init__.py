@@ -49,7 +49,7 @@ class _Opt(C.Structure):
     _fields_ = [("tol", C.c_double), ("hs_enable", C.c_int32), ("hs_min_depth", C.c_int32),
                 ("hs_iters", C.c_int32), ("root_depth", C.c_int32), ("max_depth", C.c_int32),
                 ("order", C.c_int32), ("order_seed", C.c_uint64), ("max_boxes", C.c_int64),
-                ("centred", C.c_int32)]
+                ("centred", C.c_int32), ("krawczyk", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -83,6 +83,7 @@ def _load():
             lib.orc_jacobian.argtypes = [C.POINTER(_Sys), vp, vp, vp, vp]
             lib.orc_gj_inverse.argtypes = [C.c_int, vp, vp]
             lib.orc_hs_step.argtypes = [C.POINTER(_Sys), vp, vp, vp, vp]
+            lib.orc_kr_step.argtypes = [C.POINTER(_Sys), vp, vp, vp, vp, vp, vp]
             lib.orc_centred.argtypes = [C.POINTER(_Sys), vp, vp, vp, vp]
             lib.orc_clusters.argtypes = [C.c_int, C.c_int64, vp, vp, vp]
             lib.orc_clusters.restype = C.c_int64
@@ -109,7 +110,7 @@ class _SysHolder:
 
 
 def solve(s, box_lo=None, box_hi=None, tol=None, hs_enable=True, hs_min_depth=0, hs_iters=1,
-          root_depth=0, max_depth=200, order=0, order_seed=0, max_boxes=0, centred=False):
+          root_depth=0, max_depth=200, order=0, order_seed=0, max_boxes=0, centred=False, krawczyk=False):
     """Run the serial solver.  Returns a dict with sorted boxes, flags, depths, stats, status."""
     lib = _load()
     h = _SysHolder(s)
@@ -117,7 +118,7 @@ def solve(s, box_lo=None, box_hi=None, tol=None, hs_enable=True, hs_min_depth=0,
     hi = np.ascontiguousarray(s.box_hi if box_hi is None else box_hi, dtype=np.float64)
     opt = _Opt(float(s.tol if tol is None else tol), int(hs_enable), int(hs_min_depth),
                int(hs_iters), int(root_depth), int(max_depth), int(order), int(order_seed),
-               int(max_boxes), int(bool(centred)))
+               int(max_boxes), int(bool(centred)), int(bool(krawczyk)))
     res = C.c_void_p()
     lib.orc_solve(C.byref(h.c), _ptr(lo), _ptr(hi), C.byref(opt), C.byref(res))
     try:
@@ -216,6 +217,20 @@ def hs_step(s, lo, hi):
     oh = hi.copy()
     rc = lib.orc_hs_step(C.byref(h.c), _ptr(lo), _ptr(hi), _ptr(ol), _ptr(oh))
     return rc, ol, oh
+
+
+def kr_step(s, lo, hi):
+    """One Krawczyk step (eq 15, 16).  Returns (status, lo', hi', k_lo, k_hi): K(X) in
+    k_lo/k_hi (status 0 or 1), X intersected with K(X) in lo'/hi' (status 0)."""
+    lib = _load()
+    h = _SysHolder(s)
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    ol, oh = lo.copy(), hi.copy()
+    kl = np.full_like(lo, -np.inf)
+    kh = np.full_like(hi, np.inf)
+    rc = lib.orc_kr_step(C.byref(h.c), _ptr(lo), _ptr(hi), _ptr(ol), _ptr(oh), _ptr(kl), _ptr(kh))
+    return rc, ol, oh, kl, kh
 
 
 def centred(s, lo, hi):

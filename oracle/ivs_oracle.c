@@ -263,19 +263,6 @@ static int gj_inverse(int n, const double *A, double *B) {
 
 static double midpoint(double lo, double hi) { return 0.5 * (lo + hi); }  /* eq 2.5, RN */
 
-/* One Gauss-Seidel sweep on the preconditioned linearisation B f(x) + B J(X)(z - x) = 0:
- *   x   = mid(X) (round to nearest, the same midpoint used to split),
- *   B   = Gauss-Jordan inverse of mid(J(X)) (mid of each entry, round to nearest),
- *   M   = B J(X), r = B F(x) (Algorithm 4: products rounded outward, the lower sum
- *         accumulated downward and the upper sum upward, u = 1..n in order),
- *   for i = 1..n (eq 21, 22):
- *     S_i = r_i + sum_{j<i} M_ij (X'_j - x_j) + sum_{j>i} M_ij (X_j - x_j)   (left fold)
- *     Y_i = x_i - S_i / M_ii  (extended division, eq 10)
- *     X'_i = hull(X_i intersected with Y_i); empty -> the box holds no root.
- * Readings: Algorithm 3's "P_i = R(x) - sum", "N_i = x_i + P_i / M_ii" has the sign of
- * r wrong and drops its index; eq 21 is followed.  When Y_i has two pieces X'_i is the
- * hull of the two intersections.  A NaN in S_i or M_ii leaves X'_i = X_i.
- * Returns 0 (out written), 1 (empty), 2 (skipped: mid(J) singular or B non-finite). */
 /* Centred (mean-value) form.  Section 2.3 eq 13 expands f about the point x:
  * f(y) = f(x) + J(xi)(y - x) with xi in X, so for every y in X and x = mid X,
  * f_i(y) lies in F_c,i(X) = f_i(x) + sum_j J_ij(X) (X_j - x_j).  Computed with the same
@@ -302,7 +289,27 @@ static void centred_form(const orc_system *s, const ivl *X, ivl *Fc) {
     free(J); free(xc); free(fx);
 }
 
-static int hs_sweep(const orc_system *s, const ivl *X, ivl *Xo) {
+/* One Gauss-Seidel sweep on the preconditioned linearisation B f(x) + B J(X)(z - x) = 0:
+ *   x   = mid(X) (round to nearest, the same midpoint used to split),
+ *   B   = Gauss-Jordan inverse of mid(J(X)) (mid of each entry, round to nearest),
+ *   M   = B J(X), r = B F(x) (Algorithm 4: products rounded outward, the lower sum
+ *         accumulated downward and the upper sum upward, u = 1..n in order),
+ *   for i = 1..n (eq 21, 22):
+ *     S_i = r_i + sum_{j<i} M_ij (X'_j - x_j) + sum_{j>i} M_ij (X_j - x_j)   (left fold)
+ *     Y_i = x_i - S_i / M_ii  (extended division, eq 10)
+ *     X'_i = hull(X_i intersected with Y_i); empty -> the box holds no root.
+ * Readings: Algorithm 3's "P_i = R(x) - sum", "N_i = x_i + P_i / M_ii" has the sign of
+ * r wrong and drops its index; eq 21 is followed.  When Y_i has two pieces X'_i is the
+ * hull of the two intersections.  A NaN in S_i or M_ii leaves X'_i = X_i.
+ * Returns 0 (out written), 1 (empty), 2 (skipped: mid(J) singular or B non-finite).
+ *
+ * With kr = 1 the contraction is Krawczyk's instead (eq 15, 16), from the same x, B, M
+ * and r: K_i = (x_i - r_i) + sum_j ((I - M)_ij (X_j - x_j)), a left fold over j = 1..n
+ * with (I - M)_ij = [d_ij, d_ij] - M_ij (d the Kronecker delta), every row from the
+ * incoming box X (no row uses another row's result), then X'_i = X_i intersected with
+ * K_i; a NaN in K_i leaves X'_i = X_i, an empty intersection in any row drops the box.
+ * K (if not NULL) receives K(X) before the intersection. */
+static int hs_sweep(const orc_system *s, const ivl *X, ivl *Xo, int kr, ivl *K) {
     int n = s->n_vars;
     size_t nn = (size_t)n * (size_t)n;
     ivl *J = (ivl *)malloc(sizeof(ivl) * nn);
@@ -340,6 +347,23 @@ static int hs_sweep(const orc_system *s, const ivl *X, ivl *Xo) {
         r[i] = acc;
     }
     for (int j = 0; j < n; j++) Xo[j] = X[j];
+    if (kr) {
+        int empty = 0;
+        for (int i = 0; i < n; i++) {
+            ivl Ki = iv_sub(xc[i], r[i]);
+            for (int j = 0; j < n; j++) {
+                ivl d = {i == j ? 1.0 : 0.0, i == j ? 1.0 : 0.0};
+                Ki = iv_add(Ki, iv_mul(iv_sub(d, M[i * n + j]), iv_sub(X[j], xc[j])));
+            }
+            if (K) K[i] = Ki;
+            if (isnan(Ki.lo) || isnan(Ki.hi)) continue;
+            double a = dmax(X[i].lo, Ki.lo), b = dmin(X[i].hi, Ki.hi);
+            if (a <= b) { Xo[i].lo = a; Xo[i].hi = b; }
+            else empty = 1;
+        }
+        status = empty;
+        goto done;
+    }
     for (int i = 0; i < n; i++) {
         ivl S = r[i];
         for (int j = 0; j < n; j++) {
@@ -538,7 +562,7 @@ int orc_solve(const orc_system *s, const double *box_lo, const double *box_hi,
             int dropped = 0;
             for (int it = 0; it < (o->hs_iters > 0 ? o->hs_iters : 1); it++) {
                 res->st.hs_applied++;
-                int rc = hs_sweep(s, X, Xn);
+                int rc = hs_sweep(s, X, Xn, o->krawczyk, NULL);
                 if (rc == 1) { dropped = 1; break; }
                 if (rc == 2) { res->st.hs_singular++; break; }
                 int changed = 0;
@@ -707,9 +731,22 @@ void orc_centred(const orc_system *s, const double *lo, const double *hi, double
 int orc_hs_step(const orc_system *s, const double *lo, const double *hi, double *out_lo, double *out_hi) {
     ivl X[16], Xo[16];
     for (int j = 0; j < s->n_vars; j++) { X[j].lo = lo[j]; X[j].hi = hi[j]; }
-    int rc = hs_sweep(s, X, Xo);
+    int rc = hs_sweep(s, X, Xo, 0, NULL);
     if (rc == 0)
         for (int j = 0; j < s->n_vars; j++) { out_lo[j] = Xo[j].lo; out_hi[j] = Xo[j].hi; }
+    return rc;
+}
+
+int orc_kr_step(const orc_system *s, const double *lo, const double *hi, double *out_lo, double *out_hi,
+                double *k_lo, double *k_hi) {
+    ivl X[16], Xo[16], K[16];
+    int n = s->n_vars;
+    for (int j = 0; j < n; j++) { X[j].lo = lo[j]; X[j].hi = hi[j]; K[j].lo = -INFINITY; K[j].hi = INFINITY; }
+    int rc = hs_sweep(s, X, Xo, 1, K);
+    if (rc != 2)
+        for (int j = 0; j < n; j++) { k_lo[j] = K[j].lo; k_hi[j] = K[j].hi; }
+    if (rc == 0)
+        for (int j = 0; j < n; j++) { out_lo[j] = Xo[j].lo; out_hi[j] = Xo[j].hi; }
     return rc;
 }
 

@@ -42,6 +42,9 @@ typedef struct {
     int64_t max_boxes;      /* work budget: boxes processed (0 = unlimited)         */
     int32_t centred;        /* 1: after the natural form, drop boxes whose centred
                                (mean-value) form excludes 0 (needs n_eqs == n_vars)  */
+    int32_t krawczyk;       /* 1: the contraction step is Krawczyk's operator
+                               intersected with the box (eq 15, 16) instead of the
+                               Gauss-Seidel sweep (eq 21, 22); same iteration rule     */
 } orc_options;
 
 /* result flags per accepted box */
@@ -116,6 +119,10 @@ int64_t orc_clusters(int n, int64_t count, const double *lo, const double *hi, i
  * Returns -1 when more than max_cells cells would be enumerated. */
 int64_t orc_backtrack(int n, int64_t count, const double *lo, const double *hi, const double *d_lo,
                       const double *d_hi, int level, int64_t max_cells, int64_t *groups);
+/* One Krawczyk step (eq 15, 16): K(X) into k_lo/k_hi (status 0 or 1), X intersected with
+ * K(X) into out_lo/out_hi (status 0).  Status as orc_hs_step. */
+int orc_kr_step(const orc_system *sys, const double *lo, const double *hi, double *out_lo, double *out_hi,
+                double *k_lo, double *k_hi);
 /* centred form of every equation over the box (n_eqs == n_vars): out[i] = F_c,i(X) */
 void orc_centred(const orc_system *sys, const double *lo, const double *hi, double *out_lo, double *out_hi);
 
