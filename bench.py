@@ -89,13 +89,16 @@ def jac_ops(s):
     return ops
 
 
-def hs_ops(s):
+def hs_ops(s, krawczyk=False):
     """One Hansen-Sengupta sweep: J(X), mid(J) (2 per entry), in-place Gauss-Jordan
     (n^2 divisions + 2 n^2 (n-1)), f(x) (thin evaluation), M = B J (4 n^3 - 2 n^2),
-    r = B f (4 n^2 - 2 n), Gauss-Seidel ((n-1) * 6 + 4 per row), midpoints 2n."""
+    r = B f (4 n^2 - 2 n), Gauss-Seidel ((n-1) * 6 + 4 per row), midpoints 2n.  With the
+    Krawczyk step instead of Gauss-Seidel: X - x once (2n), x - r (2n), and per entry
+    I - M, the product and the sum (6 n^2)."""
     n = s.n_vars
+    step = (2 * n + 2 * n + 6 * n * n) if krawczyk else n * (6 * (n - 1) + 4)
     return (jac_ops(s) + 2 * n * n + n * n + 2 * n * n * (n - 1) + eval_ops(s) + 4 * n ** 3 - 2 * n * n
-            + 4 * n * n - 2 * n + n * (6 * (n - 1) + 4) + 2 * n)
+            + 4 * n * n - 2 * n + step + 2 * n)
 
 
 # ---- measured DRAM traffic of the dominant kernel ----------------------------------------
@@ -118,8 +121,9 @@ def hs_sources_sha():
     return h.hexdigest()
 
 
-def hs_traffic(workload, kernel):
-    if workload != "n6" or kernel != "hs_n6" or HS_TRAFFIC_N6["sources_sha256"] != hs_sources_sha():
+def hs_traffic(workload, kernel, default_options=True):
+    if (workload != "n6" or kernel != "hs_n6" or not default_options
+            or HS_TRAFFIC_N6["sources_sha256"] != hs_sources_sha()):
         return None
     return HS_TRAFFIC_N6["bytes_per_launch"]
 
@@ -190,12 +194,12 @@ class ClockSampler:
 
 
 # ---- the oracle as CPU baseline / reference arm ---------------------------------------
-def oracle_sample(systems, budget_boxes, centred=False):
+def oracle_sample(systems, budget_boxes, centred=False, krawczyk=False):
     import oracle
     t = time.perf_counter()
     boxes = 0
     for s in systems:
-        r = oracle.solve(s, max_boxes=budget_boxes, centred=centred)
+        r = oracle.solve(s, max_boxes=budget_boxes, centred=centred, krawczyk=krawczyk)
         boxes += r["stats"]["boxes"]
         if time.perf_counter() - t > 60:
             break
@@ -207,18 +211,18 @@ def _oracle_subbox_worker(job):
     """One process of the all-cores oracle baseline: the serial oracle on each of its
     top-level sub-boxes, within a box budget."""
     import oracle
-    s, boxes, budget = job
+    s, boxes, budget, opts = job
     t = time.perf_counter()
     done = 0
     for lo, hi in boxes:
         if done >= budget:
             break
-        r = oracle.solve(s, box_lo=lo, box_hi=hi, max_boxes=budget - done)
+        r = oracle.solve(s, box_lo=lo, box_hi=hi, max_boxes=budget - done, **opts)
         done += r["stats"]["boxes"]
     return done, time.perf_counter() - t
 
 
-def oracle_all_cores(s, budget_per_core, cores=None):
+def oracle_all_cores(s, budget_per_core, cores=None, **opts):
     """The oracle on every host core: the initial box split once in every coordinate (2^n
     sub-boxes, dealt round-robin), one process per core (spawned: no fork after the GPU
     context exists).  Returns (boxes, wall seconds, cores)."""
@@ -230,7 +234,7 @@ def oracle_all_cores(s, budget_per_core, cores=None):
     for c in range(1 << n):
         up = np.array([(c >> j) & 1 for j in range(n)], dtype=bool)
         subs.append((np.where(up, mid, s.box_lo), np.where(up, s.box_hi, mid)))
-    jobs = [(s, subs[k::cores], budget_per_core) for k in range(cores)]
+    jobs = [(s, subs[k::cores], budget_per_core, opts) for k in range(cores)]
     ctx = mp.get_context("spawn")
     t = time.perf_counter()
     with ctx.Pool(cores) as pool:
@@ -243,10 +247,10 @@ def run_reference(args, systems, desc, rank, world):
         return
     budget = args.ref_boxes
     for _ in range(args.warmup):
-        oracle_sample(systems[:1], budget // 10, args.centred)
+        oracle_sample(systems[:1], budget // 10, args.centred, args.krawczyk)
     tot_b, tot_t = 0, 0.0
     for _ in range(args.steps):
-        b, t = oracle_sample(systems[:1], budget, args.centred)
+        b, t = oracle_sample(systems[:1], budget, args.centred, args.krawczyk)
         tot_b += b
         tot_t += t
     v = tot_b / tot_t
@@ -276,7 +280,11 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
         # batching form: the autotuner picks the sweep size and evaluation grid (outside timing)
         tuned = B.autotune(systems[: min(len(systems), 256)], trial_boxes=100_000)
         args.wave_children = int(tuned["wave_children"])
-    base_opts = {"centred_form": 1} if args.centred else {}
+    base_opts = {}
+    if args.centred:
+        base_opts["centred_form"] = 1
+    if args.krawczyk:
+        base_opts["krawczyk"] = 1
     plan = B.Plan(systems, opts=base_opts or None, stream=stream, wave_children=args.wave_children,
                   eval_blocks=(tuned or {}).get("eval_blocks", 0))       # graph path
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
@@ -416,7 +424,7 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
     dom = max(ktimes.items(), key=lambda kv: kv[1][1])
     n_steps = args.steps
     if dom[0].startswith("hs"):
-        ops = pst["hs_applied"] * np.mean([hs_ops(s) for s in systems]) * n_steps
+        ops = pst["hs_applied"] * np.mean([hs_ops(s, args.krawczyk) for s in systems]) * n_steps
         work = "FP64 ops of the Hansen-Sengupta sweeps (per-box count from the system tables)"
     elif dom[0] in ("eval", "eval64"):
         ops = pst["eval64_boxes"] * np.mean([eval_ops(s) for s in systems]) * n_steps
@@ -427,7 +435,7 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
     achieved = ops / (dom[1][1] * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": dom[0], "achieved": achieved, "peak": fp64_rate / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / (fp64_rate / 1e12),
-                "traffic": hs_traffic(args.workload, dom[0]),
+                "traffic": hs_traffic(args.workload, dom[0], not (args.centred or args.krawczyk)),
                 "op_convention": "one directed FP64 add or multiply = 1 flop (no FMA on the path)",
                 "peak_source": "measured in this run: directed __dadd_rd/__dmul_ru probe",
                 "work": work, "kernel_share": dom[1][1] / sum(v[1] for v in ktimes.values()),
@@ -450,10 +458,11 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
     if rank == 0:
         cpu = cpu_all = None
         if world == 1 and not args.no_cpu_baseline:
-            b, t = oracle_sample(systems[:1], args.cpu_boxes, args.centred)
+            b, t = oracle_sample(systems[:1], args.cpu_boxes, args.centred, args.krawczyk)
             cpu = {"value": b / t, "unit": "boxes/s", "cores": 1, "kind": "oracle",
                    "sample": f"first {b} boxes (LIFO order) of the {args.workload} solve, serial, fesetround"}
-            ba, ta, ca = oracle_all_cores(systems[0], max(1, args.cpu_boxes // 4))
+            ba, ta, ca = oracle_all_cores(systems[0], max(1, args.cpu_boxes // 4),
+                                          centred=args.centred, krawczyk=args.krawczyk)
             cpu_all = {"value": ba / ta, "unit": "boxes/s", "cores": ca, "kind": "oracle",
                        "sample": f"{ba} boxes: independent oracle processes over the 2^n top-level sub-boxes "
                                  f"of the {args.workload} solve, {max(1, args.cpu_boxes // 4)} boxes per process "
@@ -567,6 +576,8 @@ def main():
     ap.add_argument("--batched-count", type=int, default=4096)
     ap.add_argument("--centred", action="store_true",
                     help="add the centred-form exclusion test before Hansen-Sengupta")
+    ap.add_argument("--krawczyk", action="store_true",
+                    help="Krawczyk contraction (eq 15-16) instead of the Gauss-Seidel sweep")
     ap.add_argument("--only-timed", action="store_true",
                     help="time the device-resident solve only (for profiler runs)")
     args = ap.parse_args()
@@ -584,6 +595,8 @@ def main():
         systems, desc = workload(args.workload)
     if args.centred:
         desc += ", centred-form exclusion before HS"
+    if args.krawczyk:
+        desc += ", Krawczyk contraction instead of Gauss-Seidel"
     if args.impl == "reference":
         run_reference(args, systems, desc, rank, world)
         return

@@ -90,6 +90,15 @@ typedef struct ivs_options {
                                 (X_j - x_j) at x = mid X, folded over j = 1..n; a box
                                 is dropped when some F_c,i(X) excludes 0.  Needs
                                 n_eqs == n_vars.  0 (default): natural form only.       */
+    int32_t krawczyk;        /* 1: the contraction of every sweep (hs_enable, hs_min_depth,
+                                hs_iters as above) is Krawczyk's operator, Section 2.3
+                                eq 15-16: K_i = (x_i - r_i) + sum_j ((I - M)_ij (X_j -
+                                x_j)) with the sweep's x = mid X, M = B J(X), r = B f(x),
+                                folded over j = 1..n, every row from the incoming box;
+                                X_i becomes X_i intersected with K_i and the box is
+                                dropped when one intersection is empty.  The counters
+                                hs_* then count Krawczyk steps.  0 (default): the
+                                Gauss-Seidel sweep of eq 21-22.                         */
 } ivs_options;
 
 typedef struct ivs_stats {

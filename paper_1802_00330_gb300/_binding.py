@@ -31,7 +31,7 @@ class ivs_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("hs_enable", C.c_int32), ("hs_min_depth", C.c_int32),
                 ("hs_iters", C.c_int32), ("prefilter_fp32", C.c_int32), ("root_depth", C.c_int32),
                 ("max_depth", C.c_int32), ("max_boxes", C.c_int64), ("max_results", C.c_int64),
-                ("time_budget_s", C.c_double), ("centred_form", C.c_int32)]
+                ("time_budget_s", C.c_double), ("centred_form", C.c_int32), ("krawczyk", C.c_int32)]
 
 
 class ivs_stats(C.Structure):
@@ -168,7 +168,7 @@ class _SysRef:
 
 def make_options(tol=1e-6, hs_enable=True, hs_min_depth=0, hs_iters=1, prefilter_fp32=True,
                  root_depth=0, max_depth=200, max_boxes=0, max_results=0, time_budget_s=0.0,
-                 centred_form=False):
+                 centred_form=False, krawczyk=False):
     o = ivs_options()
     load().ivs_options_default(C.byref(o))
     o.tol = float(tol)
@@ -182,6 +182,7 @@ def make_options(tol=1e-6, hs_enable=True, hs_min_depth=0, hs_iters=1, prefilter
     o.max_results = int(max_results)
     o.time_budget_s = float(time_budget_s)
     o.centred_form = int(bool(centred_form))
+    o.krawczyk = int(bool(krawczyk))
     return o
 
 

@@ -233,6 +233,7 @@ void compile_system(HostTables &h, const ivs_system *s, const ivs_options *o) {
     d.shadow = 0;
     d.max_boxes = o->max_boxes;
     d.centred = o->centred_form ? 1 : 0;
+    d.krawczyk = o->krawczyk ? 1 : 0;
     pack_blob(h, bld, d, bld.poly_off[m]);
     h.sys.push_back(d);
 }

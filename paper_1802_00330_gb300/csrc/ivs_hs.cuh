@@ -92,7 +92,8 @@ struct Cfg {
     static constexpr int I_HS = I_JF + BB;           // HS sweep wanted in this pass
     static constexpr int I_CEN = I_HS + BB;          // centred-form test in this pass
     static constexpr int I_CEX = I_CEN + BB;         // the centred form excluded the box
-    static constexpr int I_RUN = I_CEX + BB;         // box takes part in the current sweep
+    static constexpr int I_RUN = I_CEX + BB;         // box takes part in the current sweep:
+                                                     // 1 Gauss-Seidel, 2 Krawczyk
     static constexpr int I_BAD = I_RUN + BB;         // singular preconditioner: sweep skipped
     static constexpr int I_EMPTY = I_BAD + BB;       // Gauss-Seidel left no point: box dropped
     static constexpr int INTS = I_EMPTY + BB;
@@ -392,7 +393,7 @@ __device__ __forceinline__ void gs_block(double *sd, int *si, int t) {
         const int i = e / BB, b = e % BB;
         sd[C::YLO + i * BB + b] = sd[C::XLO + i * BB + b];
         sd[C::YHI + i * BB + b] = sd[C::XHI + i * BB + b];
-        if (!run[b] || bad[b]) continue;
+        if (run[b] != 1 || bad[b]) continue;
 #pragma unroll
         for (int j = 0; j < N; j++) {
             if (j <= i) continue;
@@ -407,7 +408,7 @@ __device__ __forceinline__ void gs_block(double *sd, int *si, int t) {
     for (int i = 0; i < N; i++) {
         if (t < BB) {
             const int b = t;
-            if (run[b] && !bad[b] && !empty[b]) {
+            if (run[b] == 1 && !bad[b] && !empty[b]) {
                 ivd s = {sd[C::FR + (2 * i) * BB + b], sd[C::FR + (2 * i + 1) * BB + b]};
 #pragma unroll
                 for (int j = 0; j < N; j++) {
@@ -444,7 +445,7 @@ __device__ __forceinline__ void gs_block(double *sd, int *si, int t) {
         if (i + 1 < N) {
             for (int e = t; e < N * BB; e += NT) {
                 const int i2 = e / BB, b = e % BB;
-                if (i2 <= i || !run[b] || bad[b] || empty[b]) continue;
+                if (i2 <= i || run[b] != 1 || bad[b] || empty[b]) continue;
                 const double xc = sd[C::XC + i * BB + b];
                 const ivd d = iv_sub(ivd{sd[C::YLO + i * BB + b], sd[C::YHI + i * BB + b]}, ivd{xc, xc});
                 const ivd p = iv_mul(ivd{J[(2 * (i2 * N + i)) * BB + b], J[(2 * (i2 * N + i) + 1) * BB + b]}, d);
@@ -454,6 +455,43 @@ __device__ __forceinline__ void gs_block(double *sd, int *si, int t) {
             __syncthreads();
         }
     }
+}
+// Krawczyk step (eq 15-16) for the boxes with run == 2, after m_block: M = B J(X) sits in
+// J's place and r = B f(x) in f's.  Row i: K_i = (x_i - r_i) + sum_j ([d_ij, d_ij] - M_ij)
+// (X_j - x_j), folded over j = 1..n from the incoming box (rows are independent: one unit
+// per row and box), then Y_i = X_i intersected with K_i; a NaN leaves Y_i = X_i, an empty
+// intersection marks the box empty.  Runs after gs_block, which has set Y = X.
+template <int N>
+__device__ __forceinline__ void kr_block(double *sd, int *si, int t) {
+    using C = Cfg<N>;
+    constexpr int BB = C::BB, NT = C::NT;
+    const double *J = sd + C::JM;
+    const int *run = si + C::I_RUN;
+    const int *bad = si + C::I_BAD;
+    int *empty = si + C::I_EMPTY;
+    for (int e = t; e < N * BB; e += NT) {
+        const int i = e / BB, b = e % BB;
+        if (run[b] != 2 || bad[b]) continue;
+        const double xi = sd[C::XC + i * BB + b];
+        ivd k = iv_sub(ivd{xi, xi}, ivd{sd[C::FR + (2 * i) * BB + b], sd[C::FR + (2 * i + 1) * BB + b]});
+#pragma unroll
+        for (int j = 0; j < N; j++) {
+            const double dij = (i == j) ? 1.0 : 0.0;
+            const ivd g = iv_sub(ivd{dij, dij}, ivd{J[(2 * (i * N + j)) * BB + b], J[(2 * (i * N + j) + 1) * BB + b]});
+            const double xc = sd[C::XC + j * BB + b];
+            const ivd d = iv_sub(ivd{sd[C::XLO + j * BB + b], sd[C::XHI + j * BB + b]}, ivd{xc, xc});
+            k = iv_add(k, iv_mul(g, d));
+        }
+        if (d_isnan(k.lo) || d_isnan(k.hi)) continue;
+        const double lo = d_max(sd[C::XLO + i * BB + b], k.lo), hi = d_min(sd[C::XHI + i * BB + b], k.hi);
+        if (d_le(lo, hi)) {
+            sd[C::YLO + i * BB + b] = lo;
+            sd[C::YHI + i * BB + b] = hi;
+        } else {
+            atomicOr(&empty[b], 1);
+        }
+    }
+    __syncthreads();
 }
 }  // namespace hsd
 
@@ -566,7 +604,7 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
             if (owner) {
                 const int b = t;
                 const bool run = si[C::I_HS + b] && !si[C::I_CEX + b];
-                si[C::I_RUN + b] = run ? 1 : 0;
+                si[C::I_RUN + b] = run ? (a.tb.sys[si[C::I_SYS + b]].krawczyk ? 2 : 1) : 0;
                 st_app += run ? 1u : 0u;
                 if (si[C::I_CEX + b]) {
                     dropped_c = true;
@@ -577,6 +615,9 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
             gj_block<N>(sd, si, t);
             m_block<N, COOP>(sd, si, t);
             gs_block<N>(sd, si, t);
+            int any_kr = 0;
+            for (int b = 0; b < BB; b++) any_kr |= si[C::I_RUN + b] == 2;
+            if (any_kr) kr_block<N>(sd, si, t);
             if (owner && si[C::I_RUN + t]) {
                 const int b = t;
                 if (si[C::I_EMPTY + b]) {

@@ -57,6 +57,7 @@ struct DevSys {
     int32_t n_tv;          // term-combination entries (0: no per-parent table)
     int32_t centred;       // 1: centred-form exclusion test before Hansen-Sengupta
     int32_t n_cix;         // child-index entries (n_fterms << n; 0: none)
+    int32_t krawczyk;      // 1: Krawczyk contraction (eq 15-16) instead of Gauss-Seidel
 };
 
 struct DevTables {

@@ -233,6 +233,7 @@ extern "C" int ivs_solve_noalloc(const ivs_system *s, const double *box_lo, cons
     d.shadow = 0;   // plain FP32 prefilter: sound whatever the magnitudes
     d.max_boxes = o->max_boxes;
     d.centred = o->centred_form ? 1 : 0;
+    d.krawczyk = o->krawczyk ? 1 : 0;
 
     // ---- set-up, once per device (with that device current) ----
     int dev = 0;

@@ -192,3 +192,55 @@ def test_repeated_solves_reuse_and_stay_exact(gpu, orc):
     outs = gpu.solve_batch(b)
     for s, g in zip(b, outs):
         assert_same(g, expect[id(s)])
+
+
+_KR_ORACLE = {}
+
+
+def _kr_oracle(orc, key, s, **kw):
+    """Oracle results of the Krawczyk tests, computed once per system and options."""
+    if key not in _KR_ORACLE:
+        _KR_ORACLE[key] = orc.solve(s, krawczyk=True, **kw)
+    return _KR_ORACLE[key]
+
+
+@pytest.mark.parametrize("pre", [0, 1])
+def test_krawczyk_bit_exact(gpu, orc, pre):
+    """Krawczyk's contraction (eq 15-16) in place of the Gauss-Seidel sweep: same boxes,
+    flags, depths and counters as the oracle, one step or up to four per visit."""
+    systems = synth.config_batched(count=6, seed=781, n_range=(2, 5))
+    for iters in (1, 4):
+        for q, s in enumerate(systems):
+            g = gpu.solve(s, krawczyk=True, hs_iters=iters, prefilter_fp32=pre, tol=1e-4)
+            assert_same(g, _kr_oracle(orc, ("small", q, iters), s, hs_iters=iters, tol=1e-4))
+    s = synth.config_n6()
+    assert_same(gpu.solve(s, krawczyk=True, prefilter_fp32=pre), _kr_oracle(orc, ("n6",), s))
+
+
+def test_krawczyk_paper_system_n9(gpu, orc):
+    """kinema (n = 9), Krawczyk from the first round, cut at depth 2 (185k boxes, about
+    6000 steps of which some contract and some empty the box)."""
+    s = synth.load_fixture(os.path.join(GOLDEN, "kinema.txt"))
+    g = gpu.solve(s, krawczyk=True, tol=0.0, max_depth=2, max_results=1 << 16)
+    o = orc.solve(s, krawczyk=True, tol=0.0, max_depth=2)
+    assert o["stats"]["hs_contracted"] > 0 and o["stats"]["hs_empty"] > 0
+    assert_same(g, o)
+
+
+def test_krawczyk_with_centred_form_and_late_start(gpu, orc):
+    for s in synth.config_batched(count=6, seed=783, n_range=(3, 5)):
+        kw = dict(hs_iters=3, hs_min_depth=2, tol=1e-4)
+        assert_same(gpu.solve(s, krawczyk=True, centred_form=True, **kw),
+                    orc.solve(s, krawczyk=True, centred=True, **kw))
+
+
+def test_mixed_contractions_in_one_plan(gpu, orc):
+    """Systems of one plan may use different contractions: odd systems Krawczyk, even
+    ones Gauss-Seidel, in the same sweeps and the same kernel chunks."""
+    systems = synth.config_batched(count=8, seed=784, n_range=(2, 5))
+    opts = [gpu.make_options(tol=1e-4, krawczyk=(i % 2 == 1)) for i in range(len(systems))]
+    plan = gpu.Plan(systems, opts=opts)
+    plan.run()
+    for i, s in enumerate(systems):
+        assert_same(plan.result(i), orc.solve(s, krawczyk=(i % 2 == 1), tol=1e-4))
+    plan.close()

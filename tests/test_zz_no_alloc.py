@@ -64,3 +64,12 @@ def test_noalloc_rejects_oversized_system(B):
     s = synth.parse_system([f"x{j + 1}^2 - 1" for j in range(13)], 13, box=(-2, 2))
     rc, *_, msg = noalloc(B, s)
     assert rc == 1 and "n_vars" in msg
+
+
+def test_noalloc_krawczyk_matches_ivs_solve(B):
+    for s in [synth.config_n2()] + synth.config_batched(count=2, seed=2025, n_range=(3, 5)):
+        ref = B.solve(s, krawczyk=True)
+        rc, lo, hi, fl, st, msg = noalloc(B, s, krawczyk=True)
+        assert rc == ref["status"], msg
+        assert np.array_equal(lo, ref["lo"]) and np.array_equal(hi, ref["hi"])
+        assert st["boxes"] == ref["stats"]["boxes"] and st["hs_applied"] == ref["stats"]["hs_applied"]
