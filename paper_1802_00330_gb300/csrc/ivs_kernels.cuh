@@ -7,8 +7,10 @@
 //                   c is set); optional FP32 outward evaluation, then FP64 evaluation
 //                   (Definition 1-2); survivors compacted with a warp ballot into a list
 //                   per dimension n
-//   k_hs<N>       : one thread per survivor: Hansen-Sengupta sweep (Algorithm 3), then
-//                   accept (Algorithm 1 (II)) or write the box as a new parent
+//   k_hs<N>       : 32 survivors per block (narrow sweeps: per cluster of 4 blocks,
+//   k_hs_coop<N>    k_hs_coop): Hansen-Sengupta sweeps (Algorithm 3) or Krawczyk steps
+//                   (eq 15-16), then accept (Algorithm 1 (II)) or write the box as a
+//                   new parent
 //   k_commit      : moves the new parents onto the queue where the popped ones were
 #pragma once
 #include <cuda_runtime.h>
