@@ -200,3 +200,22 @@ def test_plans_on_another_thread_while_serving(B):
         assert sv.stats()["last_error"] == ""
     finally:
         sv.close()
+
+
+def test_served_options_per_request(B, orc):
+    """Requests carry their own options: Krawczyk contraction, centred form, several
+    sweeps per visit, mixed in one server with plain requests; each result equals the
+    oracle's for its options, bit for bit."""
+    systems = synth.config_batched(count=12, seed=4711, n_range=(2, 5))
+    kinds = [dict(), dict(krawczyk=True), dict(centred_form=True), dict(krawczyk=True, hs_iters=3)]
+    sv = B.Server(workspace_bytes=1 << 28, max_slots=16, wave_children=1 << 18, max_vars=8)
+    try:
+        tickets = [sv.submit(s, tol=1e-4, **kinds[i % 4]) for i, s in enumerate(systems)]
+        results = wait_all(sv, tickets)
+    finally:
+        sv.close()
+    for i, (s, r) in enumerate(zip(systems, results)):
+        k = kinds[i % 4]
+        o = orc.solve(s, tol=1e-4, krawczyk=k.get("krawczyk", False), centred=k.get("centred_form", False),
+                      hs_iters=k.get("hs_iters", 1))
+        assert same(r, o), i
