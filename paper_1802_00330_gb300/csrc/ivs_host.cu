@@ -409,7 +409,12 @@ int ivs_plan_run(ivs_plan *p) {
             *p->h_wave_limit = waves_done + chunk;
             CUDA_TRY(cudaMemcpyAsync(&a.ctl->wave_limit, p->h_wave_limit, sizeof(int64_t), cudaMemcpyHostToDevice, st));
             CUDA_TRY(cudaGraphLaunch(p->graph_exec, st));
+            CUDA_TRY(cudaEventRecord(p->ev1, st));
+            // the control block and the counters in one round trip (the counters of the
+            // last launch are the ones kept)
             CUDA_TRY(cudaMemcpyAsync(p->h_ctl, a.ctl, sizeof(WaveCtl), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaMemcpyAsync(p->h_stats.data(), a.stats, p->h_stats.size() * sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, st));
             CUDA_TRY(cudaStreamSynchronize(st));
             p->launches += (5 + nd) * (p->h_ctl->waves - waves_done);
             waves_done = p->h_ctl->waves;
@@ -455,10 +460,12 @@ int ivs_plan_run(ivs_plan *p) {
             }
         }
     }
-    CUDA_TRY(cudaEventRecord(p->ev1, st));
-    CUDA_TRY(cudaMemcpyAsync(p->h_stats.data(), a.stats, p->h_stats.size() * sizeof(unsigned long long),
-                             cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
+    if (!p->use_graph) {
+        CUDA_TRY(cudaEventRecord(p->ev1, st));
+        CUDA_TRY(cudaMemcpyAsync(p->h_stats.data(), a.stats, p->h_stats.size() * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
     CUDA_TRY(cudaEventElapsedTime(&p->last_ms, p->ev0, p->ev1));
     p->run_status = status;
     if (status == IVS_ERR_NOMEM) return fail(status, "work queue full: raise workspace or lower wave size");
@@ -508,12 +515,11 @@ int ivs_plan_result(ivs_plan *p, int32_t s, ivs_result **out) {
     if (total > 0) {
         CUDA_TRY(cudaMemcpyAsync(flags.data(), o.flags + base, total * 4, cudaMemcpyDeviceToHost, p->stream));
         CUDA_TRY(cudaMemcpyAsync(depth.data(), o.depth + base, total * 4, cudaMemcpyDeviceToHost, p->stream));
-        for (int j = 0; j < n; j++) {
-            CUDA_TRY(cudaMemcpyAsync(lo.data() + (size_t)j * total, o.lo + (size_t)j * o.cap + base, total * 8,
-                                     cudaMemcpyDeviceToHost, p->stream));
-            CUDA_TRY(cudaMemcpyAsync(hi.data() + (size_t)j * total, o.hi + (size_t)j * o.cap + base, total * 8,
-                                     cudaMemcpyDeviceToHost, p->stream));
-        }
+        // coordinate j of entry base + i at j * cap + base + i: one strided copy per array
+        CUDA_TRY(cudaMemcpy2DAsync(lo.data(), (size_t)total * 8, o.lo + base, (size_t)o.cap * 8, (size_t)total * 8,
+                                   (size_t)n, cudaMemcpyDeviceToHost, p->stream));
+        CUDA_TRY(cudaMemcpy2DAsync(hi.data(), (size_t)total * 8, o.hi + base, (size_t)o.cap * 8, (size_t)total * 8,
+                                   (size_t)n, cudaMemcpyDeviceToHost, p->stream));
         CUDA_TRY(cudaStreamSynchronize(p->stream));
     }
     std::unique_ptr<ivs_result> r(new (std::nothrow) ivs_result());
