@@ -22,6 +22,7 @@ from fractions import Fraction as Q
 import numpy as np
 import pytest
 
+import _dyadic as D
 from paper_1802_00330_gb300 import synth
 
 
@@ -48,50 +49,12 @@ def test_square_minus_two_worked_example(orc):
     assert ol[0] < math.sqrt(2.0) < oh[0]
 
 
-def _const(v):
-    v = float(v)
-    return f" - {v!r}" if v >= 0 else f" + {-v!r}"
-
-
-def _exact_residual(s, pt):
-    """f(pt) of the parsed system in exact rational arithmetic (checks the test's text)."""
-    out = []
-    for i in range(s.n_eqs):
-        acc = Q(0)
-        for t in s.terms_of(i):
-            assert s.coef_lo[t] == s.coef_hi[t]
-            m = Q(float(s.coef_lo[t]))
-            for j in range(s.n_vars):
-                m *= pt[j] ** int(s.exps[t, j])
-            acc += m
-        out.append(acc)
-    return out
-
-
-def _linear_system(rng, n):
-    while True:
-        a = [[rng.randint(-4, 4) for _ in range(n)] for _ in range(n)]
-        for i in range(n):
-            a[i][i] = rng.choice([-1, 1]) * rng.randint(n + 3, n + 6)   # diagonally dominant
-        if np.linalg.cond(np.array(a, float)) < 50 and not np.allclose(a, np.transpose(a)):
-            break
-    z = [Q(rng.randint(-64, 64), 32) for _ in range(n)]
-    c = [sum(a[i][j] * z[j] for j in range(n)) for i in range(n)]
-    lines = []
-    for i in range(n):
-        terms = [f"{a[i][j]}*x{j + 1}" for j in range(n) if a[i][j]]
-        lines.append(" + ".join(terms).replace("+ -", "- ") + _const(c[i]))
-    s = synth.parse_system(lines, n)
-    assert all(v == 0 for v in _exact_residual(s, z))
-    return s, z
-
-
 @pytest.mark.parametrize("n", [2, 3, 5])
 def test_linear_system_is_one_newton_step(orc, n):
     """f = A z - c: J(X) = A, B = A^-1 to rounding, so K(X) collapses onto the solution."""
     rng = random.Random(100 + n)
     for _ in range(6):
-        s, z = _linear_system(rng, n)
+        s, z = D.linear_system(rng, n)
         lo = np.array([float(zj) - rng.choice([0.25, 0.5, 0.75]) for zj in z])
         hi = lo + 1.0
         rc, ol, oh, kl, kh = orc.kr_step(s, lo, hi)
@@ -102,60 +65,17 @@ def test_linear_system_is_one_newton_step(orc, n):
             assert (ol[j], oh[j]) == (kl[j], kh[j])
 
 
-def _quadratic_system(rng, n):
-    """f_i = sum_j a_ij x_j + b_i x_i^2 - c_i with the root z; every number dyadic."""
-    a = [[rng.randint(-3, 3) for _ in range(n)] for _ in range(n)]
-    for i in range(n):
-        a[i][i] = rng.choice([-1, 1]) * rng.randint(n + 2, n + 5)
-    bq = [Q(rng.choice([-2, -1, 1, 2]), 2) for _ in range(n)]
-    z = [Q(rng.randint(-48, 48), 32) for _ in range(n)]
-    c = [sum(a[i][j] * z[j] for j in range(n)) + bq[i] * z[i] ** 2 for i in range(n)]
-    lines = []
-    for i in range(n):
-        terms = [f"{a[i][j]}*x{j + 1}" for j in range(n) if a[i][j]]
-        terms.append(f"{float(bq[i])!r}*x{i + 1}^2")
-        lines.append(" + ".join(terms).replace("+ -", "- ") + _const(c[i]))
-    s = synth.parse_system(lines, n)
-    assert all(v == 0 for v in _exact_residual(s, z))
-    return s, a, bq, c, z
-
-
-def _iv_mul_point(p, lo, hi):
-    u, v = p * lo, p * hi
-    return (min(u, v), max(u, v))
-
-
 def _exact_krawczyk(a, bq, c, B, lo, hi):
     """K(X) of eq 15 in exact rational interval arithmetic (x the exact midpoint)."""
     n = len(a)
-    X = [(Q(float(lo[j])), Q(float(hi[j]))) for j in range(n)]
-    x = [(l + h) / 2 for l, h in X]
-    J = [[None] * n for _ in range(n)]
-    for i in range(n):
-        for j in range(n):
-            if i != j:
-                J[i][j] = (Q(a[i][j]), Q(a[i][j]))
-            else:
-                e = sorted([a[i][i] + 2 * bq[i] * X[i][0], a[i][i] + 2 * bq[i] * X[i][1]])
-                J[i][j] = (e[0], e[1])
-    fx = [sum(a[i][j] * x[j] for j in range(n)) + bq[i] * x[i] ** 2 - c[i] for i in range(n)]
-    Bq = [[Q(float(B[i, u])) for u in range(n)] for i in range(n)]
+    X, x, J, M, r = D.exact_preconditioned(a, bq, c, B, lo, hi)
     K = []
     for i in range(n):
-        r = sum(Bq[i][u] * fx[u] for u in range(n))
-        klo = khi = x[i] - r
+        k = (x[i] - r[i], x[i] - r[i])
         for j in range(n):
-            mlo = mhi = Q(0)
-            for u in range(n):
-                p = _iv_mul_point(Bq[i][u], *J[u][j])
-                mlo += p[0]
-                mhi += p[1]
-            d = 1 if i == j else 0
-            g = max(abs(d - mhi), abs(d - mlo))      # (I - M)_ij times the symmetric X_j - x_j
-            hw = (X[j][1] - X[j][0]) / 2
-            klo -= g * hw
-            khi += g * hw
-        K.append((klo, khi))
+            d = Q(1 if i == j else 0)
+            k = D.iv_add(k, D.iv_mul(D.iv_sub((d, d), M[i][j]), D.iv_sub(X[j], (x[j], x[j]))))
+        K.append(k)
     return K, J
 
 
@@ -163,7 +83,7 @@ def _exact_krawczyk(a, bq, c, B, lo, hi):
 def test_quadratic_systems_exact_enclosure(orc, n):
     rng = random.Random(7000 + n)
     for _ in range(8):
-        s, a, bq, c, z = _quadratic_system(rng, n)
+        s, a, bq, c, z = D.quadratic_system(rng, n)
         lo = np.array([float(zj) - rng.randint(1, 24) / 64 for zj in z])
         hi = np.array([float(zj) + rng.randint(1, 24) / 64 for zj in z])
         jl, jh = orc.jacobian(s, lo, hi)
@@ -200,7 +120,7 @@ def test_solve_finds_planted_roots(orc, n):
     encloses the planted root."""
     rng = random.Random(900 + n)
     for _ in range(3):
-        s, a, bq, c, z = _quadratic_system(rng, n)
+        s, a, bq, c, z = D.quadratic_system(rng, n)
         box_lo = np.full(n, -4.0)
         box_hi = np.full(n, 4.0)
         r = orc.solve(s, box_lo=box_lo, box_hi=box_hi, tol=1e-6, krawczyk=True, hs_iters=4)
