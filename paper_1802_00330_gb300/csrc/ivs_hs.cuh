@@ -456,6 +456,7 @@ __device__ __forceinline__ void gs_block(double *sd, int *si, int t) {
         }
     }
 }
+
 // Krawczyk step (eq 15-16) for the boxes with run == 2, after m_block: M = B J(X) sits in
 // J's place and r = B f(x) in f's.  Row i: K_i = (x_i - r_i) + sum_j ([d_ij, d_ij] - M_ij)
 // (X_j - x_j), folded over j = 1..n from the incoming box (rows are independent: one unit
