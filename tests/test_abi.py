@@ -101,3 +101,62 @@ def test_server_without_gpu_fails_loudly(lib):
     with pytest.raises(B.IvsError) as e:
         B.Server(workspace_bytes=1 << 26, max_slots=4)
     assert e.value.status == 5
+
+
+STRUCTS = ["ivs_system", "ivs_options", "ivs_stats", "ivs_plan_cfg", "ivs_server_cfg", "ivs_server_stats",
+           "ivs_kernel_time"]
+
+
+def header_struct_fields(name):
+    """Field names of `typedef struct name { ... } name;` in declaration order."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    m = re.search(r"typedef\s+struct\s+" + name + r"\s*\{(.*?)\}\s*" + name + r"\s*;", text, flags=re.S)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        mm = re.match(r"((?:const\s+)?(?:unsigned\s+)?[A-Za-z_]\w*(?:\s+const)?)\s+(.*)$", decl, flags=re.S)
+        for d in mm.group(2).split(","):
+            fields.append(re.sub(r"\[.*\]", "", d).replace("*", "").strip())
+    return fields
+
+
+def test_binding_structs_have_the_header_fields():
+    from paper_1802_00330_gb300 import _binding as B
+    for name in STRUCTS:
+        assert [f for f, _ in getattr(B, name)._fields_] == header_struct_fields(name), name
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes mirror of a header struct has the C compiler's size and field offsets
+    (a field added on one side only would shift everything after it)."""
+    import shutil
+    import subprocess
+    from paper_1802_00330_gb300 import _binding as B
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "ivsolve.h"', "int main(void) {"]
+    for name in STRUCTS:
+        cls = getattr(B, name)
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln.strip():
+            sname, field, val = ln.split()
+            got[(sname, field)] = int(val)
+    for name in STRUCTS:
+        cls = getattr(B, name)
+        assert got[(name, "size")] == C.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
