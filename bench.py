@@ -340,6 +340,7 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
     t_dev = float(np.sum(step_t))
     if dist:
         t_dev, boxes_all = reduce_over_ranks(t_dev, boxes, device="cuda")
+        _, launches = reduce_over_ranks(0.0, launches, device="cuda")   # every rank's kernels
     else:
         boxes_all = boxes
     value = boxes_all / t_dev
@@ -383,11 +384,16 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
         b.synchronize()
         t64.append(a.elapsed_time(b) / 1e3)
         b64 += plan64.stats()["boxes"]
+    t64_total = float(np.sum(t64))
+    if dist:
+        t64_total, b64 = reduce_over_ranks(t64_total, b64, device="cuda")
     r64 = plan64.result(0)
     assert np.array_equal(r64["lo"], ref["lo"]) and np.array_equal(r64["hi"], ref["hi"])
     plan64.close()
 
     # e2e through the public host API: host system in, host boxes out
+    if dist:
+        td.barrier()
     s0 = systems[0]
     e2e_t = []
     e2e_boxes = 0
@@ -408,8 +414,11 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
             e2e_t.append(time.perf_counter() - t0)
             e2e_boxes += sum(o["stats"]["boxes"] for o in outs)
             d2h = sum(o["lo"].nbytes + o["hi"].nbytes + o["flags"].nbytes + o["depth"].nbytes for o in outs)
-    e2e = {"value": e2e_boxes / float(np.sum(e2e_t)), "unit": "boxes/s", "h2d_bytes_per_step": int(h2d),
-           "d2h_bytes_per_step": int(d2h)}
+    e2e_time = float(np.sum(e2e_t))
+    if dist:   # whole job: every rank's boxes over the slowest rank's time
+        e2e_time, e2e_boxes = reduce_over_ranks(e2e_time, e2e_boxes, device="cuda")
+    e2e = {"value": e2e_boxes / e2e_time, "unit": "boxes/s", "h2d_bytes_per_step": int(h2d * world),
+           "d2h_bytes_per_step": int(d2h * world)}
 
     # per-kernel device time: the same solve through the host loop with CUDA events
     # around every stage (a graph body cannot hold event nodes), over the same K steps
@@ -489,8 +498,8 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
                        "parallelism": f"replicas x{world}"},
             "systems_per_s": sys_per_s,
             "boxes_per_step": boxes / args.steps,
-            "plain_fp64_path": {"value": b64 / float(np.sum(t64)), "unit": "boxes/s",
-                                "ms_per_step": 1e3 * float(np.mean(t64))},
+            "plain_fp64_path": {"value": b64 / t64_total, "unit": "boxes/s",
+                                "ms_per_step": 1e3 * t64_total / len(t64)},
             "e2e": e2e,
             "gpu_launches": int(launches),
             "roofline": roofline, "prefilter_roofline": prefilter_roofline,
