@@ -157,11 +157,20 @@ def reduce_over_ranks(t_dev, boxes, device="cpu"):
 
 # ---- clocks --------------------------------------------------------------------------
 class ClockSampler:
+    """nvidia-smi samples (every 200 ms) over a timed region.  start() returns once the
+    first sample is in and stop() once one more has come in, so a region shorter than the
+    sampling period still has the samples that bracket it."""
+
     def __init__(self, index=0):
         self.index = index
         self.rows = []
         self.proc = None
         self.thread = None
+
+    def _wait_rows(self, n, timeout_s):
+        t_end = time.time() + timeout_s
+        while len(self.rows) < n and time.time() < t_end and self.proc.poll() is None:
+            time.sleep(0.005)
 
     def start(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -176,6 +185,7 @@ class ClockSampler:
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        self._wait_rows(1, 3.0)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -183,6 +193,7 @@ class ClockSampler:
 
     def stop(self):
         if self.proc:
+            self._wait_rows(len(self.rows) + 1, 1.0)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
