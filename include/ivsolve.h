@@ -299,14 +299,16 @@ int ivs_backtrack(int32_t n_vars, int64_t count, const double *lo, const double 
                   const double *box_hi, int32_t level, int64_t max_cells, int64_t *n_cells, int64_t *n_groups);
 
 /* ---- allocation-free solve ------------------------------------------------------ */
-/* No counterpart in the paper: an entry point for callers that cannot allocate.  Code
- * that runs while a CUDA stream is being captured into a graph, processes whose device
- * memory belongs to a pool they must not bypass, and allocation-free real-time loops
- * cannot call cudaMalloc.  ivs_solve_noalloc solves one system like ivs_solve but
- * allocates nothing: every byte of device scratch comes from one fixed file-scope
- * __device__ array of IVS_NOALLOC_SCRATCH_BYTES inside the library (present on every
- * GPU that loads the library, until the process exits), host work uses static buffers
- * and the stack, and it calls no cudaMalloc, cudaFree or other allocating routine.
+/* No counterpart in the paper: an entry point for callers that cannot allocate.
+ * Processes whose device memory belongs to a pool they must not bypass (a framework's
+ * caching allocator, a serving engine that reserved the GPU's memory up front), plug-ins
+ * and callbacks running inside another runtime that forbids allocation, and real-time
+ * loops that cannot afford cudaMalloc's implicit synchronisation cannot call cudaMalloc.
+ * ivs_solve_noalloc solves one system like ivs_solve but allocates nothing: every byte
+ * of device scratch comes from one fixed file-scope __device__ array of
+ * IVS_NOALLOC_SCRATCH_BYTES inside the library (present on every GPU that loads the
+ * library, until the process exits), host work uses static buffers and the stack, and it
+ * calls no cudaMalloc, cudaFree or other allocating routine.
  *
  * Limits of the fixed buffers: n_vars <= 12, a compiled term table (equations plus
  * Jacobian) of at most 48 KiB / 2048 terms, and at most 16384 boxes held as results.
@@ -315,11 +317,13 @@ int ivs_backtrack(int32_t n_vars, int64_t count, const double *lo, const double 
  * boxes than out_cap or 16384 returns IVS_ERR_BUDGET with the first ones.
  *
  * Inputs (host pointers) as for ivs_solve.  stream: a cudaStream_t or NULL (the legacy
- * default stream); the call returns after the solve.  Outputs (host memory owned by the
- * caller): out_lo / out_hi receive up to out_cap boxes of n_vars doubles, row-major and
- * sorted as in ivs_result_boxes; out_flags (may be NULL) their IVS_BOX_* flags;
- * *out_count the number written; stats (may be NULL) the counters; errbuf (may be NULL)
- * a message of at most errbuf_len bytes.  Returns an IVS_* status.
+ * default stream); the call waits on it between sweeps and returns after the solve, so
+ * a stream in capture mode is rejected with IVS_ERR_INVALID.  Outputs (host memory
+ * owned by the caller): out_lo / out_hi receive up to out_cap boxes of n_vars doubles,
+ * row-major and sorted as in ivs_result_boxes; out_flags (may be NULL) their IVS_BOX_*
+ * flags; *out_count the number written; stats (may be NULL) the counters; errbuf (may be
+ * NULL) a message of at most errbuf_len bytes, also kept as ivs_last_error().  Returns
+ * an IVS_* status.
  *
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.  Every

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -17,10 +18,15 @@
 namespace ivs {
 namespace host {
 
-thread_local std::string g_last_error;
+// fixed per-thread buffer: recording an error allocates nothing
+thread_local char g_last_error[512];
+
+void set_error_text(const char *msg) {
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg ? msg : "");
+}
 
 int fail(int status, const std::string &msg) {
-    g_last_error = msg;
+    set_error_text(msg.c_str());
     return status;
 }
 
@@ -71,7 +77,7 @@ void add_term(SysBuild &b, double clo, double chi, const uint8_t *e, int n) {
             b.fac.push_back((uint8_t)((j << 4) | e[j]));
             cnt++;
         }
-    b.tinfo.push_back((start << 5) | cnt | (clo == chi ? kTermPoint : 0u));
+    b.tinfo.push_back(term_info(start, cnt, clo, chi));
 }
 
 // packs a built system into the blob arena and fills the blob fields of d
@@ -238,7 +244,7 @@ void compile_system(HostTables &h, const ivs_system *s, const ivs_options *o) {
     h.sys.push_back(d);
 }
 
-const char *last_error() { return g_last_error.c_str(); }
+const char *last_error() { return g_last_error; }
 
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }

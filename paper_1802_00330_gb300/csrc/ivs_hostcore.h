@@ -28,6 +28,7 @@ void fill_sorted(ivs_result *r, int n, int64_t total, const std::vector<double> 
                  const std::vector<int32_t> &flags, const std::vector<int32_t> &depth);
 
 int fail(int status, const std::string &msg);   // records the thread's error text, returns status
+void set_error_text(const char *msg);            // records the thread's error text (no allocation)
 const char *last_error();
 
 #define CUDA_TRY(expr)                                                                   \

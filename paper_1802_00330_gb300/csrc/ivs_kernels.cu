@@ -8,9 +8,7 @@
 // roundings), so the sorted result set is identical to the serial solver's.
 #include <cuda_runtime.h>
 
-#include <map>
 #include <mutex>
-#include <tuple>
 
 #include "ivs_internal.h"
 #include "ivs_interval.cuh"
@@ -671,16 +669,28 @@ static cudaError_t launch_hs(const SweepArgs &a, int n, int num_sms, cudaStream_
     }
 }
 
+// The answers live in a fixed table (no heap allocation, so the allocation-free entry
+// point may launch through here too); when it is full, further shapes are queried each
+// time instead of cached.
 int coop_clusters_cached(const void *func, int num_sms, int threads, size_t smem, cudaError_t *err) {
+    struct Known {
+        const void *func;
+        int num_sms, threads, dev, clusters;
+        size_t smem;
+    };
+    constexpr int kSlots = 512;
     static std::mutex mu;
-    static std::map<std::tuple<const void *, int, int, size_t, int>, int> known;
+    static Known known[kSlots];
+    static int used = 0;
     int dev = 0;
     *err = cudaGetDevice(&dev);
     if (*err != cudaSuccess) return 0;
-    const auto key = std::make_tuple(func, num_sms, threads, smem, dev);
     std::lock_guard<std::mutex> lk(mu);
-    auto it = known.find(key);
-    if (it != known.end()) return it->second;
+    for (int i = 0; i < used; i++) {
+        const Known &k = known[i];
+        if (k.func == func && k.num_sms == num_sms && k.threads == threads && k.smem == smem && k.dev == dev)
+            return k.clusters;
+    }
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3((unsigned)((num_sms / 4) * 4));
     lc.blockDim = dim3((unsigned)threads);
@@ -688,7 +698,7 @@ int coop_clusters_cached(const void *func, int num_sms, int threads, size_t smem
     int nc = 0;
     *err = cudaOccupancyMaxActiveClusters(&nc, func, &lc);
     if (*err != cudaSuccess) return 0;
-    known[key] = nc;
+    if (used < kSlots) known[used++] = Known{func, num_sms, threads, dev, nc, smem};
     return nc;
 }
 

@@ -1,14 +1,15 @@
 // ivs_noalloc.cu -- a solve entry point that allocates nothing.
 //
-// Some callers cannot allocate device memory: code running while a CUDA stream is being
-// captured into a graph, processes whose device memory is owned by a pool they must not
-// bypass, or allocation-free real-time loops.  ivs_solve_noalloc serves them: it runs the
-// same sweep kernels as ivs_solve, but every byte of device scratch (tables, queue,
-// staging, survivor lists, result list, counters) comes from one file-scope __device__
-// array of IVS_NOALLOC_SCRATCH_BYTES, and the host side uses fixed static buffers and
-// the stack.  It calls no cudaMalloc, cudaFree, cudaMallocHost or other allocating
-// routine.  The array exists on every GPU that loads the library, until the process
-// exits.
+// Some callers cannot allocate device memory: processes whose device memory belongs to a
+// pool they must not bypass (a framework's caching allocator, or a serving engine that
+// reserved the GPU's memory up front), plug-ins and callbacks that run inside another
+// runtime which forbids allocation, and real-time loops that cannot afford cudaMalloc's
+// implicit synchronisation.  ivs_solve_noalloc serves them: it runs the same sweep
+// kernels as ivs_solve, but every byte of device scratch (tables, queue, staging,
+// survivor lists, result list, counters) comes from one file-scope __device__ array of
+// IVS_NOALLOC_SCRATCH_BYTES, and the host side uses fixed static buffers and the stack.
+// It calls no cudaMalloc, cudaFree, cudaMallocHost or other allocating routine.  The
+// array exists on every GPU that loads the library, until the process exits.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -18,6 +19,7 @@
 #include <mutex>
 
 #include "../../include/ivsolve.h"
+#include "ivs_hostcore.h"
 #include "ivs_internal.h"
 #include "ivs_kernels.cuh"
 #include "ivs_tab.cuh"
@@ -42,13 +44,16 @@ WaveCtl g_ctl;                          // host copy of the sweep control block
 char *g_errbuf = nullptr;               // the current call's message buffer (caller's)
 int32_t g_errlen = 0;
 
+// the message goes to the caller's buffer and to the thread's ivs_last_error() text
 int err(int status, const char *msg) {
     if (g_errbuf && g_errlen > 0) std::snprintf(g_errbuf, (size_t)g_errlen, "%s", msg);
+    host::set_error_text(msg);
     return status;
 }
 int err_cuda(const char *what, cudaError_t e) {
-    if (g_errbuf && g_errlen > 0) std::snprintf(g_errbuf, (size_t)g_errlen, "%s: %s", what, cudaGetErrorString(e));
-    return IVS_ERR_CUDA;
+    char msg[256];
+    std::snprintf(msg, sizeof(msg), "%s: %s", what, cudaGetErrorString(e));
+    return err(IVS_ERR_CUDA, msg);
 }
 
 // exact outward products and float conversions (error-free product: Dekker's TwoProduct)
@@ -116,7 +121,7 @@ bool pack_static(const ivs_system *s, DevSys &d) {
                 f++;
                 cnt++;
             }
-        const uint32_t info = (start << 5) | cnt;
+        const uint32_t info = term_info(start, cnt, clo, chi);
         std::memcpy(g_host_blob + L.tinfo + 4u * t, &info, 4);
         t++;
     }, [&]() { poly_off[++p] = t; });
@@ -248,6 +253,13 @@ extern "C" int ivs_solve_noalloc(const ivs_system *s, const double *box_lo, cons
     }
     char *base = (char *)g_scratch_addr[dev];
     cudaStream_t st = (cudaStream_t)stream_ptr;
+    // the loop below waits on the stream between sweeps and copies into pageable host
+    // memory, which a stream in capture mode does not allow
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    ce = cudaStreamIsCapturing(st, &cap);
+    if (ce != cudaSuccess) return err_cuda("cudaStreamIsCapturing", ce);
+    if (cap != cudaStreamCaptureStatusNone)
+        return err(IVS_ERR_INVALID, "ivs_solve_noalloc: the stream is in capture mode (the call synchronises it)");
     int sms = 0;
     ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (ce != cudaSuccess) return err_cuda("cudaDeviceGetAttribute", ce);

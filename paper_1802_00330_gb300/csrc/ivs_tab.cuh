@@ -47,6 +47,11 @@ __host__ __device__ inline BlobLayout blob_layout(int T, int P, int F, int TF = 
 constexpr uint32_t kTermPoint = 1u << 31;
 __host__ __device__ inline int term_nf(uint32_t info) { return (int)(info & 31u); }
 __host__ __device__ inline int term_f0(uint32_t info) { return (int)((info & ~kTermPoint) >> 5); }
+// the info word of a term whose factors start at `start` (count `cnt`) with coefficient
+// interval [clo, chi]; every packer of term tables uses this one encoding
+__host__ __device__ inline uint32_t term_info(uint32_t start, uint32_t cnt, double clo, double chi) {
+    return (start << 5) | cnt | (clo == chi ? kTermPoint : 0u);
+}
 
 struct SysTab {
     const float4 *cs;        // {rd32(c_lo), ru32(c_lo), rd32(c_hi), ru32(c_hi)}

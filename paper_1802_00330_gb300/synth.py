@@ -244,6 +244,29 @@ def config_served(duration_s: float = 60.0, rate: float = 2000.0,
     return np.array(times), systems
 
 
+def served_systems(count: int, seed: int = SEED_BASE + 5, n_range=(3, 12)):
+    """The first `count` requests of the served recipe (n ~ U{3..12}, degree <= 4, 6-14
+    monomials per equation, integer coefficients in [-5,5], planted root on the 1/8 grid
+    in [-1.5,1.5]^n, box [-2,2]^n, tol 1e-6), drawn from a generator of their own so
+    that request k is the same system whatever arrival process carries it."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in range(count):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        nm = len(monomials(n, 4)) + 1
+        eq_terms = [min(int(rng.integers(6, 15)), nm) for _ in range(n)]
+        root = _grid_root(rng, n, Fraction(3, 2))
+        out.append(_make_system(n, eq_terms, 4, _int_coef(rng), root, rng, 2, 1e-6, f"request_{s}_n{n}"))
+    return out
+
+
+def poisson_arrivals(count: int, rate: float, seed: int = SEED_BASE + 6):
+    """Arrival times (seconds from 0) of `count` requests of a Poisson stream of mean
+    `rate` requests per second: cumulative exponential gaps from a seeded generator."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=count))
+
+
 def random_boxes(rng, n, count, lo=-4.0, hi=4.0, min_w=1e-6, max_w=2.0):
     """Random boxes inside [lo,hi]^n with widths log-uniform in [min_w, max_w]
     (dyadic-friendly values are not forced; endpoints are arbitrary doubles)."""

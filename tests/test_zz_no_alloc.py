@@ -1,10 +1,13 @@
 """ivs_solve_noalloc: the allocation-free solve, for callers that cannot call cudaMalloc
-(code running under stream capture, pool-managed processes, allocation-free loops).
+(processes whose device memory belongs to a pool they must not bypass, plug-ins running
+inside a runtime that forbids allocation, real-time loops that cannot afford cudaMalloc's
+implicit synchronisation).
 
 Called through the C ABI, it must return exactly what ivs_solve returns (the same sorted
 boxes, flags and processed-box count), twice in a row (the fixed scratch keeps the last
 call's contents, so the second call checks that everything that must start at zero is
 cleared), and it must reject systems too large for its fixed buffers with a clear error.
+After its first call on a device it must leave the device's free memory unchanged.
 This file is collected last so that a failure here comes after every other test ran.
 """
 
@@ -73,3 +76,66 @@ def test_noalloc_krawczyk_matches_ivs_solve(B):
         assert rc == ref["status"], msg
         assert np.array_equal(lo, ref["lo"]) and np.array_equal(hi, ref["hi"])
         assert st["boxes"] == ref["stats"]["boxes"] and st["hs_applied"] == ref["stats"]["hs_applied"]
+
+
+def test_noalloc_leaves_device_memory_unchanged(B):
+    """The defining property: after a first call (which looks up the scratch address),
+    a solve changes the device's free memory by nothing."""
+    import torch
+    s = synth.config_n6()
+    rc, *_ = noalloc(B, s)
+    assert rc == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        rc, lo, *_ = noalloc(B, s)
+        assert rc == 0 and len(lo) > 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_noalloc_budget_when_the_output_is_too_small(B):
+    """Two roots, room for one box: IVS_ERR_BUDGET with one of ivs_solve's boxes."""
+    s = synth.config_n2()
+    ref = B.solve(s)
+    rc, lo, hi, fl, st, msg = noalloc(B, s, out_cap=1)
+    assert rc == 3 and len(lo) == 1
+    assert any(np.array_equal(lo[0], a) and np.array_equal(hi[0], b) for a, b in zip(ref["lo"], ref["hi"]))
+    assert st["accepted"] == ref["stats"]["accepted"] == 2
+
+
+def _many_terms_system(n=12, terms_per_eq=180):
+    """n equations of `terms_per_eq` monomials of degree <= 3: more terms than the fixed
+    table holds (2048)."""
+    rng = np.random.default_rng(5)
+    mons = synth.monomials(n, 3)
+    exps, offs = [], [0]
+    for _ in range(n):
+        idx = rng.choice(len(mons), size=terms_per_eq, replace=False)
+        exps += [mons[q] for q in sorted(idx)]
+        offs.append(len(exps))
+    coef = rng.integers(1, 5, size=len(exps)).astype(np.float64)
+    return synth.PolySystem(n_vars=n, n_eqs=n, eq_offsets=np.array(offs, np.int32), coef_lo=coef,
+                            coef_hi=coef.copy(), exps=np.array(exps, np.uint8), box_lo=np.full(n, -1.0),
+                            box_hi=np.full(n, 1.0), tol=1e-3)
+
+
+def test_noalloc_rejects_an_oversized_term_table(B):
+    rc, *_, msg = noalloc(B, _many_terms_system())
+    assert rc == 1 and "term table" in msg
+
+
+def test_noalloc_error_text_without_a_buffer(B):
+    """With errbuf = NULL the message is still kept as ivs_last_error()."""
+    lib = B.load()
+    s = synth.parse_system([f"x{j + 1}^2 - 1" for j in range(13)], 13, box=(-2, 2))
+    ref = B._SysRef(s)
+    o = B.make_options(tol=s.tol)
+    lo = np.zeros((4, 13))
+    hi = np.zeros((4, 13))
+    cnt = C.c_int64(-1)
+    rc = lib.ivs_solve_noalloc(C.byref(ref.c), B._ptr(ref.lo), B._ptr(ref.hi), C.byref(o), None,
+                               B._ptr(lo), B._ptr(hi), None, 4, C.byref(cnt), None, None, 0)
+    assert rc == 1 and cnt.value == 0
+    assert "n_vars" in lib.ivs_last_error().decode()
