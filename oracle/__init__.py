@@ -49,14 +49,15 @@ class _Opt(C.Structure):
     _fields_ = [("tol", C.c_double), ("hs_enable", C.c_int32), ("hs_min_depth", C.c_int32),
                 ("hs_iters", C.c_int32), ("root_depth", C.c_int32), ("max_depth", C.c_int32),
                 ("order", C.c_int32), ("order_seed", C.c_uint64), ("max_boxes", C.c_int64),
-                ("centred", C.c_int32), ("krawczyk", C.c_int32)]
+                ("centred", C.c_int32), ("krawczyk", C.c_int32), ("split_mode", C.c_int32),
+                ("gap_split", C.c_int32)]
 
 
 class _Stats(C.Structure):
     _fields_ = [("boxes", C.c_int64), ("excluded_eval", C.c_int64), ("hs_applied", C.c_int64),
                 ("hs_empty", C.c_int64), ("hs_contracted", C.c_int64), ("hs_singular", C.c_int64),
                 ("accepted", C.c_int64), ("unsplittable", C.c_int64), ("split", C.c_int64),
-                ("max_depth_seen", C.c_int32), ("excluded_centred", C.c_int64)]
+                ("max_depth_seen", C.c_int32), ("excluded_centred", C.c_int64), ("gap_splits", C.c_int64)]
 
 
 def _load():
@@ -84,6 +85,7 @@ def _load():
             lib.orc_gj_inverse.argtypes = [C.c_int, vp, vp]
             lib.orc_hs_step.argtypes = [C.POINTER(_Sys), vp, vp, vp, vp]
             lib.orc_kr_step.argtypes = [C.POINTER(_Sys), vp, vp, vp, vp, vp, vp]
+            lib.orc_hs_gap_step.argtypes = [C.POINTER(_Sys), vp, vp, vp, vp, vp, vp, vp]
             lib.orc_centred.argtypes = [C.POINTER(_Sys), vp, vp, vp, vp]
             lib.orc_clusters.argtypes = [C.c_int, C.c_int64, vp, vp, vp]
             lib.orc_clusters.restype = C.c_int64
@@ -110,7 +112,8 @@ class _SysHolder:
 
 
 def solve(s, box_lo=None, box_hi=None, tol=None, hs_enable=True, hs_min_depth=0, hs_iters=1,
-          root_depth=0, max_depth=200, order=0, order_seed=0, max_boxes=0, centred=False, krawczyk=False):
+          root_depth=0, max_depth=200, order=0, order_seed=0, max_boxes=0, centred=False, krawczyk=False,
+          split_mode=0, gap_split=False):
     """Run the serial solver.  Returns a dict with sorted boxes, flags, depths, stats, status."""
     lib = _load()
     h = _SysHolder(s)
@@ -118,7 +121,7 @@ def solve(s, box_lo=None, box_hi=None, tol=None, hs_enable=True, hs_min_depth=0,
     hi = np.ascontiguousarray(s.box_hi if box_hi is None else box_hi, dtype=np.float64)
     opt = _Opt(float(s.tol if tol is None else tol), int(hs_enable), int(hs_min_depth),
                int(hs_iters), int(root_depth), int(max_depth), int(order), int(order_seed),
-               int(max_boxes), int(bool(centred)), int(bool(krawczyk)))
+               int(max_boxes), int(bool(centred)), int(bool(krawczyk)), int(split_mode), int(bool(gap_split)))
     res = C.c_void_p()
     lib.orc_solve(C.byref(h.c), _ptr(lo), _ptr(hi), C.byref(opt), C.byref(res))
     try:
@@ -231,6 +234,21 @@ def kr_step(s, lo, hi):
     kh = np.full_like(hi, np.inf)
     rc = lib.orc_kr_step(C.byref(h.c), _ptr(lo), _ptr(hi), _ptr(ol), _ptr(oh), _ptr(kl), _ptr(kh))
     return rc, ol, oh, kl, kh
+
+
+def hs_gap_step(s, lo, hi):
+    """One Gauss-Seidel sweep with the two-box split of a gap.  Returns (status, boxes,
+    gap_row): status 0 one box, 1 empty, 2 skipped (singular), 3 two boxes (the lower and
+    the upper piece of coordinate gap_row); boxes = list of (lo, hi)."""
+    lib = _load()
+    h = _SysHolder(s)
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    ol, oh, ol2, oh2 = lo.copy(), hi.copy(), lo.copy(), hi.copy()
+    g = np.zeros(1, np.int32)
+    rc = lib.orc_hs_gap_step(C.byref(h.c), _ptr(lo), _ptr(hi), _ptr(ol), _ptr(oh), _ptr(ol2), _ptr(oh2), _ptr(g))
+    boxes = [] if rc in (1, 2) else [(ol, oh)] + ([(ol2, oh2)] if rc == 3 else [])
+    return rc, boxes, int(g[0])
 
 
 def centred(s, lo, hi):

@@ -308,8 +308,17 @@ static void centred_form(const orc_system *s, const ivl *X, ivl *Fc) {
  * with (I - M)_ij = [d_ij, d_ij] - M_ij (d the Kronecker delta), every row from the
  * incoming box X (no row uses another row's result), then X'_i = X_i intersected with
  * K_i; a NaN in K_i leaves X'_i = X_i, an empty intersection in any row drops the box.
- * K (if not NULL) receives K(X) before the intersection. */
-static int hs_sweep(const orc_system *s, const ivl *X, ivl *Xo, int kr, ivl *K) {
+ * K (if not NULL) receives K(X) before the intersection.
+ *
+ * With gap = 1 (the variant after eq 22: split the box where the extended division leaves
+ * a gap, instead of taking the hull) a Gauss-Seidel row whose Y_i meets X_i in two
+ * pieces records the gap between them, RN(lower end of the upper piece - upper end of
+ * the lower piece); later rows still use the hull.  If some row left a gap wider than 0,
+ * the row with the widest one (the first of equal ones) splits the swept box in two:
+ * Xo takes the lower piece in that coordinate and Xo2 the upper one (*gap_row = the
+ * row), and the return value is 3. */
+static int hs_sweep(const orc_system *s, const ivl *X, ivl *Xo, int kr, ivl *K, int gap, ivl *Xo2,
+                    int *gap_row) {
     int n = s->n_vars;
     size_t nn = (size_t)n * (size_t)n;
     ivl *J = (ivl *)malloc(sizeof(ivl) * nn);
@@ -364,6 +373,9 @@ static int hs_sweep(const orc_system *s, const ivl *X, ivl *Xo, int kr, ivl *K) 
         status = empty;
         goto done;
     }
+    double best_gap = 0;
+    int best_row = -1;
+    ivl gap_lower = {0, 0}, gap_upper = {0, 0};
     for (int i = 0; i < n; i++) {
         ivl S = r[i];
         for (int j = 0; j < n; j++) {
@@ -372,18 +384,30 @@ static int hs_sweep(const orc_system *s, const ivl *X, ivl *Xo, int kr, ivl *K) 
         }
         ivl D = M[i * n + i];
         if (isnan(S.lo) || isnan(S.hi) || isnan(D.lo) || isnan(D.hi)) continue;
-        ivl Np[2];
+        ivl Np[2], piece[2];
         int np = iv_extdiv(S, D, Np);
         double lo = INFINITY, hi = -INFINITY;
         int any = 0;
         for (int q = 0; q < np; q++) {
             ivl Y = iv_sub(xc[i], Np[q]);
             double a = dmax(X[i].lo, Y.lo), b = dmin(X[i].hi, Y.hi);
-            if (a <= b) { lo = dmin(lo, a); hi = dmax(hi, b); any = 1; }
+            if (a <= b) { lo = dmin(lo, a); hi = dmax(hi, b); piece[any].lo = a; piece[any].hi = b; any++; }
         }
         if (!any) { status = 1; goto done; }
+        if (gap && any == 2) {
+            int u = piece[1].lo < piece[0].lo ? 0 : 1;   /* the upper piece */
+            double g = piece[u].lo - piece[1 - u].hi;     /* round to nearest */
+            if (g > best_gap) { best_gap = g; best_row = i; gap_lower = piece[1 - u]; gap_upper = piece[u]; }
+        }
         Xo[i].lo = lo;
         Xo[i].hi = hi;
+    }
+    if (best_row >= 0) {
+        for (int j = 0; j < n; j++) Xo2[j] = Xo[j];
+        Xo[best_row] = gap_lower;
+        Xo2[best_row] = gap_upper;
+        *gap_row = best_row;
+        status = 3;
     }
 done:
     free(J); free(M); free(A); free(B); free(xc); free(fx); free(r);
@@ -474,12 +498,14 @@ static int validate(const orc_system *s, const double *lo, const double *hi, con
     }
     for (int j = 0; j < s->n_vars; j++) if (!isfinite(lo[j]) || !isfinite(hi[j]) || lo[j] > hi[j]) return 1;
     if ((o->hs_enable || o->centred) && s->n_eqs != s->n_vars) return 1;
+    if (o->split_mode < 0 || o->split_mode > 1 || o->gap_split < 0 || o->gap_split > 1) return 1;
     if (!(o->tol >= 0) || !isfinite(o->tol) || o->hs_iters < 0 || o->max_depth < 0) return 1;
     return 0;
 }
 
-static int cmp_box_n;
-static const double *cmp_lo, *cmp_hi;
+/* comparator context of the final sort: per thread, so solves may run concurrently */
+static _Thread_local int cmp_box_n;
+static _Thread_local const double *cmp_lo, *cmp_hi;
 static int cmp_idx(const void *pa, const void *pb) {
     int64_t a = *(const int64_t *)pa, b = *(const int64_t *)pb;
     for (int j = 0; j < cmp_box_n; j++) {
@@ -489,6 +515,58 @@ static int cmp_idx(const void *pa, const void *pb) {
         x = cmp_hi[a * cmp_box_n + j]; y = cmp_hi[b * cmp_box_n + j];
         if (x < y) return -1;
         if (x > y) return 1;
+    }
+    return 0;
+}
+
+/* Algorithm 1 termination (II) and the split for a box that survived evaluation and
+ * contraction: accept it at the desired width, or when its widest coordinate cannot be
+ * split in doubles, or return it flagged at the depth limit, or push its children --
+ * Algorithm 2's 2^n children (child c takes the upper half of coordinate j when bit j
+ * of c is set) or, with split_mode = 1, the two halves of its widest coordinate (the
+ * first of equal widths).  Returns 0, or 1 when memory ran out. */
+static int finish_box(orc_result *res, stack_t_ *q, const ivl *X, int n, int32_t depth, const orc_options *o,
+                      double *mid, double *clo, double *chi, int *depth_cut) {
+    double w = 0;
+    int jw = 0;
+    for (int j = 0; j < n; j++) {
+        double wj = X[j].hi - X[j].lo;
+        if (wj > w) { w = wj; jw = j; }
+    }
+    if (w <= o->tol) {
+        if (result_push(res, X, ORC_ACCEPT_WIDTH, depth)) return 1;
+        res->st.accepted++;
+        return 0;
+    }
+    for (int j = 0; j < n; j++) mid[j] = midpoint(X[j].lo, X[j].hi);
+    if (mid[jw] == X[jw].lo || mid[jw] == X[jw].hi) {
+        if (result_push(res, X, ORC_ACCEPT_UNSPLITTABLE, depth)) return 1;
+        res->st.accepted++;
+        res->st.unsplittable++;
+        return 0;
+    }
+    if (depth + 1 > o->max_depth) {
+        /* depth cut: the box is returned unsplit, flagged, and the solve is incomplete */
+        if (result_push(res, X, ORC_ACCEPT_DEPTH_LIMIT, depth)) return 1;
+        *depth_cut = 1;
+        return 0;
+    }
+    res->st.split++;
+    if (o->split_mode == 1) {
+        for (int c = 0; c < 2; c++) {
+            for (int j = 0; j < n; j++) { clo[j] = X[j].lo; chi[j] = X[j].hi; }
+            if (c) clo[jw] = mid[jw];
+            else chi[jw] = mid[jw];
+            if (stack_push(q, n, clo, chi, depth + 1)) return 1;
+        }
+        return 0;
+    }
+    for (int64_t c = 0; c < ((int64_t)1 << n); c++) {
+        for (int j = 0; j < n; j++) {
+            if ((c >> j) & 1) { clo[j] = mid[j]; chi[j] = X[j].hi; }
+            else { clo[j] = X[j].lo; chi[j] = mid[j]; }
+        }
+        if (stack_push(q, n, clo, chi, depth + 1)) return 1;
     }
     return 0;
 }
@@ -505,13 +583,14 @@ int orc_solve(const orc_system *s, const double *box_lo, const double *box_hi,
     stack_t_ q = {0};
     ivl *X = (ivl *)malloc(sizeof(ivl) * (size_t)n);
     ivl *Xn = (ivl *)malloc(sizeof(ivl) * (size_t)n);
+    ivl *X2 = (ivl *)malloc(sizeof(ivl) * (size_t)n);
     ivl *F = (ivl *)malloc(sizeof(ivl) * (size_t)m);
     double *clo = (double *)malloc(sizeof(double) * (size_t)n);
     double *chi = (double *)malloc(sizeof(double) * (size_t)n);
     double *mid = (double *)malloc(sizeof(double) * (size_t)n);
     uint64_t rng = o->order_seed;
     int status = ORC_OK, depth_cut = 0;
-    if (!X || !Xn || !F || !clo || !chi || !mid || stack_push(&q, n, box_lo, box_hi, o->root_depth)) {
+    if (!X || !Xn || !X2 || !F || !clo || !chi || !mid || stack_push(&q, n, box_lo, box_hi, o->root_depth)) {
         status = ORC_ERR_NOMEM;
         goto done;
     }
@@ -558,13 +637,22 @@ int orc_solve(const orc_system *s, const double *box_lo, const double *box_hi,
         }
 
         /* Algorithm 1 step (III): Hansen-Sengupta contraction */
+        int two = 0;   /* the sweep split the box at a gap: X and X2 go on */
         if (o->hs_enable && depth >= o->hs_min_depth) {
             int dropped = 0;
             for (int it = 0; it < (o->hs_iters > 0 ? o->hs_iters : 1); it++) {
                 res->st.hs_applied++;
-                int rc = hs_sweep(s, X, Xn, o->krawczyk, NULL);
+                int gap_row = -1;
+                int rc = hs_sweep(s, X, Xn, o->krawczyk, NULL, o->gap_split && !o->krawczyk, X2, &gap_row);
                 if (rc == 1) { dropped = 1; break; }
                 if (rc == 2) { res->st.hs_singular++; break; }
+                if (rc == 3) {
+                    res->st.hs_contracted++;
+                    res->st.gap_splits++;
+                    memcpy(X, Xn, sizeof(ivl) * (size_t)n);
+                    two = 1;
+                    break;
+                }
                 int changed = 0;
                 for (int j = 0; j < n; j++)
                     if (Xn[j].lo != X[j].lo || Xn[j].hi != X[j].hi) changed = 1;
@@ -578,40 +666,11 @@ int orc_solve(const orc_system *s, const double *box_lo, const double *box_hi,
         }
         res->depth_kept[dslot]++;
 
-        /* Algorithm 1 termination (II): accept at the desired width */
-        double w = 0;
-        int jw = 0;
-        for (int j = 0; j < n; j++) {
-            double wj = X[j].hi - X[j].lo;
-            if (wj > w) { w = wj; jw = j; }
-        }
-        if (w <= o->tol) {
-            if (result_push(res, X, ORC_ACCEPT_WIDTH, depth)) { status = ORC_ERR_NOMEM; goto done; }
-            res->st.accepted++;
-            continue;
-        }
-        for (int j = 0; j < n; j++) mid[j] = midpoint(X[j].lo, X[j].hi);
-        if (mid[jw] == X[jw].lo || mid[jw] == X[jw].hi) {
-            if (result_push(res, X, ORC_ACCEPT_UNSPLITTABLE, depth)) { status = ORC_ERR_NOMEM; goto done; }
-            res->st.accepted++;
-            res->st.unsplittable++;
-            continue;
-        }
-        if (depth + 1 > o->max_depth) {
-            /* depth cut: the box is returned unsplit, flagged, and the solve is incomplete */
-            if (result_push(res, X, ORC_ACCEPT_DEPTH_LIMIT, depth)) { status = ORC_ERR_NOMEM; goto done; }
-            depth_cut = 1;
-            continue;
-        }
-        /* Algorithm 2: split every coordinate at its midpoint; child c takes the upper
-         * half of coordinate j when bit j of c is set. */
-        res->st.split++;
-        for (int64_t c = 0; c < ((int64_t)1 << n); c++) {
-            for (int j = 0; j < n; j++) {
-                if ((c >> j) & 1) { clo[j] = mid[j]; chi[j] = X[j].hi; }
-                else { clo[j] = X[j].lo; chi[j] = mid[j]; }
-            }
-            if (stack_push(&q, n, clo, chi, depth + 1)) { status = ORC_ERR_NOMEM; goto done; }
+        /* Algorithm 1 termination (II) and Algorithm 2's split, for X (and X2) */
+        if (finish_box(res, &q, X, n, depth, o, mid, clo, chi, &depth_cut)) { status = ORC_ERR_NOMEM; goto done; }
+        if (two && finish_box(res, &q, X2, n, depth, o, mid, clo, chi, &depth_cut)) {
+            status = ORC_ERR_NOMEM;
+            goto done;
         }
     }
 done:
@@ -643,7 +702,7 @@ done:
         free(idx); free(nl); free(nh); free(nf); free(nd);
     }
     free(q.lo); free(q.hi); free(q.depth);
-    free(X); free(Xn); free(F); free(clo); free(chi); free(mid);
+    free(X); free(Xn); free(X2); free(F); free(clo); free(chi); free(mid);
     return res->status;
 }
 
@@ -731,9 +790,23 @@ void orc_centred(const orc_system *s, const double *lo, const double *hi, double
 int orc_hs_step(const orc_system *s, const double *lo, const double *hi, double *out_lo, double *out_hi) {
     ivl X[16], Xo[16];
     for (int j = 0; j < s->n_vars; j++) { X[j].lo = lo[j]; X[j].hi = hi[j]; }
-    int rc = hs_sweep(s, X, Xo, 0, NULL);
+    int rc = hs_sweep(s, X, Xo, 0, NULL, 0, NULL, NULL);
     if (rc == 0)
         for (int j = 0; j < s->n_vars; j++) { out_lo[j] = Xo[j].lo; out_hi[j] = Xo[j].hi; }
+    return rc;
+}
+
+int orc_hs_gap_step(const orc_system *s, const double *lo, const double *hi, double *out_lo, double *out_hi,
+                    double *out2_lo, double *out2_hi, int32_t *gap_row) {
+    ivl X[16], Xo[16], X2[16];
+    int g = -1;
+    for (int j = 0; j < s->n_vars; j++) { X[j].lo = lo[j]; X[j].hi = hi[j]; }
+    int rc = hs_sweep(s, X, Xo, 0, NULL, 1, X2, &g);
+    if (rc == 0 || rc == 3)
+        for (int j = 0; j < s->n_vars; j++) { out_lo[j] = Xo[j].lo; out_hi[j] = Xo[j].hi; }
+    if (rc == 3)
+        for (int j = 0; j < s->n_vars; j++) { out2_lo[j] = X2[j].lo; out2_hi[j] = X2[j].hi; }
+    if (gap_row) *gap_row = g;
     return rc;
 }
 
@@ -742,7 +815,7 @@ int orc_kr_step(const orc_system *s, const double *lo, const double *hi, double 
     ivl X[16], Xo[16], K[16];
     int n = s->n_vars;
     for (int j = 0; j < n; j++) { X[j].lo = lo[j]; X[j].hi = hi[j]; K[j].lo = -INFINITY; K[j].hi = INFINITY; }
-    int rc = hs_sweep(s, X, Xo, 1, K);
+    int rc = hs_sweep(s, X, Xo, 1, K, 0, NULL, NULL);
     if (rc != 2)
         for (int j = 0; j < n; j++) { k_lo[j] = K[j].lo; k_hi[j] = K[j].hi; }
     if (rc == 0)

@@ -45,6 +45,11 @@ typedef struct {
     int32_t krawczyk;       /* 1: the contraction step is Krawczyk's operator
                                intersected with the box (eq 15, 16) instead of the
                                Gauss-Seidel sweep (eq 21, 22); same iteration rule     */
+    int32_t split_mode;     /* 0: Algorithm 2's split of every coordinate (2^n children);
+                               1: bisection of the widest coordinate only (2 children)  */
+    int32_t gap_split;      /* 1: a Gauss-Seidel sweep whose extended division leaves a
+                               gap inside X_i returns two boxes, one per piece (the
+                               widest such gap over the rows), instead of the hull      */
 } orc_options;
 
 /* result flags per accepted box */
@@ -70,6 +75,7 @@ typedef struct {
     int64_t split;
     int32_t max_depth_seen;
     int64_t excluded_centred;  /* dropped because some centred form F_c,i(X) excludes 0 */
+    int64_t gap_splits;     /* sweeps that returned two boxes (gap_split = 1)         */
 } orc_stats;
 
 typedef struct orc_result orc_result;
@@ -123,6 +129,11 @@ int64_t orc_backtrack(int n, int64_t count, const double *lo, const double *hi, 
  * K(X) into out_lo/out_hi (status 0).  Status as orc_hs_step. */
 int orc_kr_step(const orc_system *sys, const double *lo, const double *hi, double *out_lo, double *out_hi,
                 double *k_lo, double *k_hi);
+/* One Gauss-Seidel sweep with the two-box split of a gap (gap_split = 1): status as
+ * orc_hs_step, or 3 when the sweep returns two boxes -- out (the lower piece of
+ * coordinate *gap_row) and out2 (the upper piece); the other coordinates are equal. */
+int orc_hs_gap_step(const orc_system *sys, const double *lo, const double *hi, double *out_lo, double *out_hi,
+                    double *out2_lo, double *out2_hi, int32_t *gap_row);
 /* centred form of every equation over the box (n_eqs == n_vars): out[i] = F_c,i(X) */
 void orc_centred(const orc_system *sys, const double *lo, const double *hi, double *out_lo, double *out_hi);
 
