@@ -99,6 +99,18 @@ typedef struct ivs_options {
                                 dropped when one intersection is empty.  The counters
                                 hs_* then count Krawczyk steps.  0 (default): the
                                 Gauss-Seidel sweep of eq 21-22.                         */
+    int32_t split_mode;      /* 0 (default): Algorithm 2's split of every coordinate at its
+                                midpoint (2^n children).  1: bisection of the widest
+                                coordinate only (the first of equal widths; 2 children,
+                                depth + 1 per bisection)                                 */
+    int32_t gap_split;       /* 1: a Gauss-Seidel sweep whose extended division (eq 10)
+                                leaves a gap inside X_i returns two boxes, one per piece,
+                                at the row with the widest gap RN(lower end of the upper
+                                piece - upper end of the lower piece) (the first of equal
+                                ones; later rows use the hull), instead of the hull
+                                (Section 2.3, after eq 22).  Both boxes then take the
+                                accept / split step; the visit's sweeps stop there.
+                                Ignored with krawczyk = 1.                              */
 } ivs_options;
 
 typedef struct ivs_stats {
@@ -121,6 +133,7 @@ typedef struct ivs_stats {
     double queue_ms;            /* served requests: submit -> admission                */
     double solve_ms;            /* served requests: admission -> result ready          */
     int64_t excluded_centred;   /* dropped by the centred form (centred_form = 1)      */
+    int64_t gap_splits;         /* sweeps that returned two boxes (gap_split = 1)      */
 } ivs_stats;
 
 typedef struct ivs_result ivs_result;
@@ -224,8 +237,8 @@ int ivs_probe_rate(int32_t kind, int32_t device, double *ops_per_s, double *ms);
  * arrive while others run are admitted between sweeps (one sweep = Algorithm 2's
  * evaluation of every child of the popped parents, then Algorithm 3 and the accept /
  * split step) as soon as a slot and queue memory are free: each request owns a region of
- * 64 * 2^n queue entries (reserve_factor scales it), and requests wait, in arrival order,
- * until one is free.  Every sweep gives each request in flight a fair share of its
+ * 64 * 2^n queue entries (reserve_factor scales it; at least min_region_entries), and
+ * requests wait, in arrival order, until one is free.  Every sweep gives each request in flight a fair share of its
  * children, and their sweeps share kernels.  A system is solved when none of its
  * boxes remain in the queue; its result (the same as ivs_solve's, bit for bit: each box's
  * fate depends only on the box) is then ready for ivs_server_poll / ivs_server_wait.
@@ -245,6 +258,10 @@ typedef struct ivs_server_cfg {
     int32_t sweeps_per_step;  /* sweeps between admissions / completion checks (0 = 2)    */
     int32_t device;           /* CUDA device ordinal                                      */
     double reserve_factor;    /* scales the per-request queue reservation (0 = 1)         */
+    int64_t min_region_entries; /* smallest queue region of a request, in entries (0 = no
+                                 minimum beyond 64 * 2^n): a region that is more than half
+                                 full gives its request one parent per sweep, so a larger
+                                 region lets small requests finish in fewer sweeps        */
 } ivs_server_cfg;
 
 typedef struct ivs_server_stats {

@@ -31,7 +31,8 @@ class ivs_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("hs_enable", C.c_int32), ("hs_min_depth", C.c_int32),
                 ("hs_iters", C.c_int32), ("prefilter_fp32", C.c_int32), ("root_depth", C.c_int32),
                 ("max_depth", C.c_int32), ("max_boxes", C.c_int64), ("max_results", C.c_int64),
-                ("time_budget_s", C.c_double), ("centred_form", C.c_int32), ("krawczyk", C.c_int32)]
+                ("time_budget_s", C.c_double), ("centred_form", C.c_int32), ("krawczyk", C.c_int32),
+                ("split_mode", C.c_int32), ("gap_split", C.c_int32)]
 
 
 class ivs_stats(C.Structure):
@@ -40,7 +41,8 @@ class ivs_stats(C.Structure):
                 ("hs_singular", C.c_int64), ("accepted", C.c_int64), ("unsplittable", C.c_int64),
                 ("split", C.c_int64), ("max_depth_seen", C.c_int32), ("waves", C.c_int32),
                 ("device_ms", C.c_double), ("launches", C.c_int64), ("eval64_boxes", C.c_int64),
-                ("kept_shadow", C.c_int64), ("queue_ms", C.c_double), ("solve_ms", C.c_double), ("excluded_centred", C.c_int64)]
+                ("kept_shadow", C.c_int64), ("queue_ms", C.c_double), ("solve_ms", C.c_double), ("excluded_centred", C.c_int64),
+                ("gap_splits", C.c_int64)]
 
 
 class ivs_plan_cfg(C.Structure):
@@ -52,7 +54,7 @@ class ivs_plan_cfg(C.Structure):
 class ivs_server_cfg(C.Structure):
     _fields_ = [("workspace_bytes", C.c_size_t), ("wave_children", C.c_int64), ("results_per_slot", C.c_int64),
                 ("max_slots", C.c_int32), ("max_vars", C.c_int32), ("sweeps_per_step", C.c_int32),
-                ("device", C.c_int32), ("reserve_factor", C.c_double)]
+                ("device", C.c_int32), ("reserve_factor", C.c_double), ("min_region_entries", C.c_int64)]
 
 
 class ivs_server_stats(C.Structure):
@@ -168,7 +170,7 @@ class _SysRef:
 
 def make_options(tol=1e-6, hs_enable=True, hs_min_depth=0, hs_iters=1, prefilter_fp32=True,
                  root_depth=0, max_depth=200, max_boxes=0, max_results=0, time_budget_s=0.0,
-                 centred_form=False, krawczyk=False):
+                 centred_form=False, krawczyk=False, split_mode=0, gap_split=False):
     o = ivs_options()
     load().ivs_options_default(C.byref(o))
     o.tol = float(tol)
@@ -183,6 +185,8 @@ def make_options(tol=1e-6, hs_enable=True, hs_min_depth=0, hs_iters=1, prefilter
     o.time_budget_s = float(time_budget_s)
     o.centred_form = int(bool(centred_form))
     o.krawczyk = int(bool(krawczyk))
+    o.split_mode = int(split_mode)
+    o.gap_split = int(bool(gap_split))
     return o
 
 
@@ -304,14 +308,15 @@ class Server:
     poll or wait for their results."""
 
     def __init__(self, workspace_bytes=0, wave_children=0, results_per_slot=0, max_slots=0, max_vars=0,
-                 sweeps_per_step=0, device=0, reserve_factor=0.0):
+                 sweeps_per_step=0, device=0, reserve_factor=0.0, min_region_entries=0):
         lib = load()
         self._lib = lib
         cfg = ivs_server_cfg()
         lib.ivs_server_cfg_default(C.byref(cfg))
         for k, v in (("workspace_bytes", workspace_bytes), ("wave_children", wave_children),
                      ("results_per_slot", results_per_slot), ("max_slots", max_slots), ("max_vars", max_vars),
-                     ("sweeps_per_step", sweeps_per_step), ("reserve_factor", reserve_factor)):
+                     ("sweeps_per_step", sweeps_per_step), ("reserve_factor", reserve_factor),
+                     ("min_region_entries", min_region_entries)):
             if v:
                 setattr(cfg, k, v)
         cfg.device = int(device)

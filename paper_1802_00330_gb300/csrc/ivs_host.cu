@@ -479,6 +479,7 @@ static void fill_stats(const ivs_plan *p, int s, ivs_stats *st) {
     st->excluded_prefilter += (int64_t)v[ST_EXCL_PREFILTER];
     st->excluded_eval += (int64_t)v[ST_EXCL_EVAL];
     st->excluded_centred += (int64_t)v[ST_EXCL_CENTRED];
+    st->gap_splits += (int64_t)v[ST_GAP_SPLITS];
     st->hs_applied += (int64_t)v[ST_HS_APPLIED];
     st->hs_empty += (int64_t)v[ST_HS_EMPTY];
     st->hs_contracted += (int64_t)v[ST_HS_CONTRACTED];

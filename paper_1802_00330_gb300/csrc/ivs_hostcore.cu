@@ -172,6 +172,8 @@ int validate(const ivs_system *s, const double *lo, const double *hi, const ivs_
     if (o->hs_iters < 0 || o->max_depth < 0 || o->max_depth > 0xFFF0 || o->root_depth < 0 ||
         o->root_depth > o->max_depth)
         return fail(IVS_ERR_INVALID, "bad depth / iteration options");
+    if (o->split_mode < 0 || o->split_mode > 1 || o->gap_split < 0 || o->gap_split > 1)
+        return fail(IVS_ERR_INVALID, "split_mode must be 0 or 1, gap_split 0 or 1");
     return IVS_OK;
 }
 
@@ -240,6 +242,8 @@ void compile_system(HostTables &h, const ivs_system *s, const ivs_options *o) {
     d.max_boxes = o->max_boxes;
     d.centred = o->centred_form ? 1 : 0;
     d.krawczyk = o->krawczyk ? 1 : 0;
+    d.bisect = o->split_mode == 1 ? 1 : 0;
+    d.gap_split = o->gap_split ? 1 : 0;
     pack_blob(h, bld, d, bld.poly_off[m]);
     h.sys.push_back(d);
 }

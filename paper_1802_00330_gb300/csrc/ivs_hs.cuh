@@ -377,12 +377,23 @@ __device__ __forceinline__ void m_block(double *sd, const int *si, int t) {
     }
 }
 
+// The widest gap an owner thread's Gauss-Seidel rows left (gap_split): row, width and the
+// two pieces of X_i; row -1 while there is none.  Lives in the owner's registers.
+struct GapRec {
+    bool on;
+    int row;
+    double w, llo, lhi, ulo, uhi;
+};
+
 // Gauss-Seidel (eq 21-22).  Row i folds r_i and the products M_ij (Y_j - x_j), j != i,
 // in order j = 1..n; products with j > i use the box's own coordinates and are formed
 // up front, those with j < i as soon as Y_j is final.  A product is written over M_ij,
-// which nothing reads afterwards.
+// which nothing reads afterwards.  With gr.on (the owner's box asks for the two-box
+// split) a row whose Y_i meets X_i in two pieces records its gap RN(lower end of the
+// upper piece - upper end of the lower piece) in gr when it is wider than the widest so
+// far; the row itself still takes the hull.
 template <int N>
-__device__ __forceinline__ void gs_block(double *sd, int *si, int t) {
+__device__ __forceinline__ void gs_block(double *sd, int *si, int t, GapRec &gr) {
     using C = Cfg<N>;
     constexpr int BB = C::BB, NT = C::NT;
     double *J = sd + C::JM;
@@ -423,18 +434,36 @@ __device__ __forceinline__ void gs_block(double *sd, int *si, int t) {
                     const double xlo = sd[C::XLO + i * BB + b], xhi = sd[C::XHI + i * BB + b];
                     double lo = 0.0, hi = 0.0;
                     bool any = false;
-                    for (int q = 0; q < np; q++) {
+                    double pa[2] = {0.0, 0.0}, pb[2] = {0.0, 0.0};   // the non-empty pieces
+                    int npc = 0;
+#pragma unroll
+                    for (int q = 0; q < 2; q++) {
+                        if (q >= np) continue;
                         const ivd Y = iv_sub(ivd{xc, xc}, pc[q]);
                         const double a0 = d_max(xlo, Y.lo), b0 = d_min(xhi, Y.hi);
                         if (d_le(a0, b0)) {
                             lo = any ? d_min(lo, a0) : a0;
                             hi = any ? d_max(hi, b0) : b0;
                             any = true;
+                            if (npc == 0) { pa[0] = a0; pb[0] = b0; }
+                            else { pa[1] = a0; pb[1] = b0; }
+                            npc++;
                         }
                     }
                     if (!any) {
                         empty[b] = 1;
                     } else {
+                        if (gr.on && npc == 2) {
+                            const bool zero_up = !d_le(pa[0], pa[1]);   // piece 1 starts below piece 0
+                            const double llo = zero_up ? pa[1] : pa[0], lhi = zero_up ? pb[1] : pb[0];
+                            const double ulo = zero_up ? pa[0] : pa[1], uhi = zero_up ? pb[0] : pb[1];
+                            const double g = __dsub_rn(ulo, lhi);
+                            if (g > gr.w) {
+                                gr.w = g;
+                                gr.row = i;
+                                gr.llo = llo; gr.lhi = lhi; gr.ulo = ulo; gr.uhi = uhi;
+                            }
+                        }
                         sd[C::YLO + i * BB + b] = lo;
                         sd[C::YHI + i * BB + b] = hi;
                     }
@@ -551,7 +580,12 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
         // the owners fetch their boxes: child `child` of queue entry `parent`
         bool active = false, stopped = false, dropped = false, dropped_c = false;
         int sys = 0, depth = 0, its = 0, cen = 0;
-        unsigned st_app = 0, st_con = 0, st_sing = 0;
+        unsigned st_app = 0, st_con = 0, st_sing = 0, st_gap = 0;
+        // a sweep that split the box at a gap: the upper piece of coordinate two_row
+        bool two = false;
+        int two_row = 0;
+        double two_lo = 0.0, two_hi = 0.0;
+        GapRec gr{false, -1, 0.0, 0.0, 0.0, 0.0, 0.0};
         if (owner) {
             const int b = t;
             const long long idx = base + b;
@@ -612,10 +646,15 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
                     stopped = true;
                 }
             }
+            if (owner) {
+                gr.on = si[C::I_RUN + t] == 1 && a.tb.sys[si[C::I_SYS + t]].gap_split;
+                gr.row = -1;
+                gr.w = 0.0;
+            }
             __syncthreads();
             gj_block<N>(sd, si, t);
             m_block<N, COOP>(sd, si, t);
-            gs_block<N>(sd, si, t);
+            gs_block<N>(sd, si, t, gr);
             int any_kr = 0;
             for (int b = 0; b < BB; b++) any_kr |= si[C::I_RUN + b] == 2;
             if (any_kr) kr_block<N>(sd, si, t);
@@ -637,6 +676,20 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
                         sd[C::XHI + j * BB + b] = yhi;
                         sd[C::XC + j * BB + b] = midpoint_rn(ylo, yhi);
                     }
+                    if (gr.row >= 0) {
+                        // two boxes at the widest gap: this one keeps the lower piece, the
+                        // upper one takes the accept / split step after it; no more sweeps
+                        sd[C::XLO + gr.row * BB + b] = gr.llo;
+                        sd[C::XHI + gr.row * BB + b] = gr.lhi;
+                        sd[C::XC + gr.row * BB + b] = midpoint_rn(gr.llo, gr.lhi);
+                        two = true;
+                        two_row = gr.row;
+                        two_lo = gr.ulo;
+                        two_hi = gr.uhi;
+                        changed = true;
+                        st_gap = 1;
+                        stopped = true;
+                    }
                     st_con += changed ? 1u : 0u;
                     // iterated until the contraction stalls (Section 2.3): a sweep that
                     // leaves the box unchanged would leave it unchanged again
@@ -646,13 +699,22 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
             __syncthreads();
         }
         // Algorithm 1 termination (II) and the split, by warp 0 (lane b owns box b); in the
-        // cooperative form only the cluster's first CTA writes
+        // cooperative form only the cluster's first CTA writes.  A box split at a gap takes
+        // a second pass with the upper piece in its gap coordinate.
         if (t < 32 && rank == 0) {
             const int b = t;
+            const int passes = __any_sync(kFull, two) ? 2 : 1;
+            for (int pass = 0; pass < passes; pass++) {
+            const bool act = active && (pass == 0 || two);
+            if (pass == 1 && two) {
+                sd[C::XLO + two_row * BB + b] = two_lo;
+                sd[C::XHI + two_row * BB + b] = two_hi;
+            }
             int fate = 0;   // 0 none / dropped, 1 accepted, 2 new parent
             int flag = 0;
+            int jw = 0;     // the widest coordinate (the first of equal widths)
             unsigned st_uns = 0, st_empty = 0, st_cex = 0;
-            if (active) {
+            if (act) {
                 const DevSys &S = a.tb.sys[sys];
                 if (dropped_c) {
                     st_cex = 1;
@@ -660,7 +722,6 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
                     st_empty = 1;
                 } else {
                     double w = 0.0;
-                    int jw = 0;
 #pragma unroll
                     for (int j = 0; j < N; j++) {
                         const double wj = __dsub_rn(sd[C::XHI + j * BB + b], sd[C::XLO + j * BB + b]);
@@ -691,7 +752,7 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
             }
             // accepted boxes, into the system's result region
             const int sys0 = __shfl_sync(kFull, sys, 0);
-            const bool uniform = __all_sync(kFull, !active || sys == sys0);
+            const bool uniform = __all_sync(kFull, !act || sys == sys0);
             {
                 const unsigned ma = __ballot_sync(kFull, fate == 1);
                 long long k = -1;
@@ -721,7 +782,9 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
                     if (flag == 4) atomicOr(stat_ptr(a, sys, ST_FLAGS), (unsigned long long)kFlagDepthCut);
                 }
             }
-            // new parents (the split midpoints are the box midpoints)
+            // new parents: the split midpoints are the box midpoints (Algorithm 2); with
+            // bisection only the widest coordinate has one (mid = hi elsewhere) and the
+            // meta word carries that coordinate
             const unsigned ms = __ballot_sync(kFull, fate == 2);
             if (ms) {
                 unsigned long long pos = 0;
@@ -730,36 +793,40 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
                 if (fate == 2) {
                     const long long k = (long long)(pos + __popc(ms & lanemask_lt()));
                     if (k < a.stage.cap) {
+                        const bool bis = a.tb.sys[sys].bisect != 0;
 #pragma unroll
                         for (int j = 0; j < N; j++) {
                             const double lo = sd[C::XLO + j * BB + b], hi = sd[C::XHI + j * BB + b];
                             a.stage.lo[j * a.stage.cap + k] = lo;
-                            a.stage.mid[j * a.stage.cap + k] = midpoint_rn(lo, hi);
+                            a.stage.mid[j * a.stage.cap + k] = (bis && j != jw) ? hi : midpoint_rn(lo, hi);
                             a.stage.hi[j * a.stage.cap + k] = hi;
                         }
                         a.stage.sys[k] = sys;
-                        a.stage.meta[k] = (uint32_t)depth & kDepthMask;
+                        a.stage.meta[k] = ((uint32_t)depth & kDepthMask) | (bis ? ((uint32_t)jw << kSplitShift) : 0u);
                     } else {
                         ctl->error = 1;
                     }
                 }
             }
             // statistics (new parents also enter the live count): one atomic per warp when
-            // the warp holds a single system
-            unsigned v[9] = {st_app, st_empty, st_con, st_sing, (fate == 1 && flag != 4) ? 1u : 0u, st_uns,
-                             fate == 2 ? 1u : 0u, fate == 2 ? 1u : 0u, st_cex};
-            const int slot[9] = {ST_HS_APPLIED, ST_HS_EMPTY, ST_HS_CONTRACTED, ST_HS_SINGULAR, ST_ACCEPTED,
-                                 ST_UNSPLITTABLE, ST_SPLIT, ST_LIVE, ST_EXCL_CENTRED};
+            // the warp holds a single system; the sweep's counters only in the first pass
+            const bool p0 = pass == 0;
+            unsigned v[10] = {p0 ? st_app : 0u, st_empty, p0 ? st_con : 0u, p0 ? st_sing : 0u,
+                              (fate == 1 && flag != 4) ? 1u : 0u, st_uns, fate == 2 ? 1u : 0u, fate == 2 ? 1u : 0u,
+                              st_cex, p0 ? st_gap : 0u};
+            const int slot[10] = {ST_HS_APPLIED, ST_HS_EMPTY, ST_HS_CONTRACTED, ST_HS_SINGULAR, ST_ACCEPTED,
+                                  ST_UNSPLITTABLE, ST_SPLIT, ST_LIVE, ST_EXCL_CENTRED, ST_GAP_SPLITS};
             if (uniform) {
 #pragma unroll
-                for (int q = 0; q < 9; q++) {
+                for (int q = 0; q < 10; q++) {
                     const unsigned tot = __reduce_add_sync(kFull, v[q]);
                     if (lane == 0 && tot) atomicAdd(stat_ptr(a, sys0, slot[q]), (unsigned long long)tot);
                 }
-            } else if (active) {
+            } else if (act) {
 #pragma unroll
-                for (int q = 0; q < 9; q++)
+                for (int q = 0; q < 10; q++)
                     if (v[q]) atomicAdd(stat_ptr(a, sys, slot[q]), (unsigned long long)v[q]);
+            }
             }
         }
         __syncthreads();   // the chunk's arrays and s_base are reused by the next chunk

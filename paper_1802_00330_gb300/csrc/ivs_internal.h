@@ -13,6 +13,11 @@ constexpr int kMaxExp = 15;
 // box that is evaluated itself, fan-out 1, not split first).
 constexpr uint32_t kRootFlag = 1u << 30;
 constexpr uint32_t kDepthMask = 0xFFFFu;
+// Bisection (split_mode 1): the coordinate a parent is split in, bits 16-19 of its meta
+// word; its queue entry holds mid_j = hi_j in every other coordinate, so child c (bit
+// `coordinate` of c) reads [lo_j, hi_j] there whatever the decoding.
+constexpr int kSplitShift = 16;
+constexpr uint32_t kSplitMask = 0xFu;
 
 // per-system statistics slots (int64 counters on the device)
 enum Stat : int {
@@ -33,6 +38,7 @@ enum Stat : int {
     ST_OUT,            // accepted boxes of the system (its result region holds min(this, out_cap))
     ST_LIVE,           // queue entries of the system (0 after a sweep: the system is solved)
     ST_EXCL_CENTRED,   // boxes the centred form dropped
+    ST_GAP_SPLITS,     // sweeps that returned two boxes at an extended-division gap
     ST_COUNT
 };
 constexpr int64_t kFlagResultOverflow = 1, kFlagDepthCut = 2, kFlagBudget = 4;
@@ -58,7 +64,24 @@ struct DevSys {
     int32_t centred;       // 1: centred-form exclusion test before Hansen-Sengupta
     int32_t n_cix;         // child-index entries (n_fterms << n; 0: none)
     int32_t krawczyk;      // 1: Krawczyk contraction (eq 15-16) instead of Gauss-Seidel
+    int32_t bisect;        // 1: widest-coordinate bisection (2 children) instead of 2^n
+    int32_t gap_split;     // 1: two boxes at an extended-division gap (Gauss-Seidel only)
 };
+
+// children of a popped queue entry: 1 for an initial box, else 2 (bisection) or 2^n
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int64_t fan_out(const DevSys &S, uint32_t meta) {
+    return (meta & kRootFlag) ? 1 : (S.bisect ? 2 : ((int64_t)1 << S.n));
+}
+// child bits of the c-th child of an entry (bit j set: upper half of coordinate j)
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline uint32_t child_bits(const DevSys &S, uint32_t meta, uint32_t c) {
+    return (S.bisect && !(meta & kRootFlag)) ? (c << ((meta >> kSplitShift) & kSplitMask)) : c;
+}
 
 struct DevTables {
     const DevSys *sys;

@@ -76,7 +76,7 @@ __device__ void wave_begin_regions(const SweepArgs &a) {
             const int64_t held = rg.rem[sl];
             if (held > 0) {
                 const bool root = held == 1 && (a.q.meta[rg.base[sl]] & kRootFlag) != 0;
-                fan = root ? 1 : (1ll << a.tb.sys[sl].n);
+                fan = fan_out(a.tb.sys[sl], root ? kRootFlag : 0u);
                 k = share / fan;
                 if (k < 1) k = 1;
                 if (k > held) k = held;
@@ -122,7 +122,7 @@ __device__ void wave_begin_regions(const SweepArgs &a) {
             rg.prefix[sl] = run;
             run += k;
             const bool root = rg.rem[sl] == 1 && (a.q.meta[rg.base[sl]] & kRootFlag) != 0;
-            kids += k * (root ? 1 : (1ll << a.tb.sys[sl].n));
+            kids += k * fan_out(a.tb.sys[sl], root ? kRootFlag : 0u);
             rg.rem[sl] -= k;
         }
         rg.prefix[S] = run;
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kBeginThreads) k_wave_begin(SweepArgs a) {
                 k = 1;
                 children = 1;
             } else {
-                const int64_t F = (int64_t)1 << a.tb.sys[0].n;
+                const int64_t F = fan_out(a.tb.sys[0], 0u);
                 k = a.wave_children / F;
                 const int64_t by_room = (a.q.cap - top) / (F - 1);
                 k = k < by_room ? k : by_room;
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kBeginThreads) k_wave_begin(SweepArgs a) {
     // entry i (0-based from the top) is queue index top - 1 - i
     auto fan_of = [&](int64_t i) -> long long {
         const int64_t e = top - 1 - i;
-        return (a.q.meta[e] & kRootFlag) ? 1 : (1ll << a.tb.sys[a.q.sys[e]].n);
+        return fan_out(a.tb.sys[a.q.sys[e]], a.q.meta[e]);
     };
     long long local = 0;
     for (int q = 0; q < kBeginPer; q++) {
@@ -472,7 +472,7 @@ __device__ __forceinline__ void eval_parent(const SweepArgs &a, WaveCtl *ctl, co
         se[5][r] = hiu;
     }
     group_sync<BLOCK>();
-    const unsigned fan = root ? 1u : (1u << n);
+    const unsigned fan = (unsigned)fan_out(S, meta);
     unsigned cnt_pre = 0, cnt_ev = 0, cnt_64 = 0, cnt_sh = 0;
     // per-parent term-combination table: when the fan-out fills warps and it fits
     const bool use_tv = S.prefilter && S.shadow && S.n_tv > 0 && S.n_tv <= a.tv_stride && fan >= 32;
@@ -484,8 +484,8 @@ __device__ __forceinline__ void eval_parent(const SweepArgs &a, WaveCtl *ctl, co
         group_sync<BLOCK>();
     }
     for (unsigned c0 = 0; c0 < fan; c0 += G) {
-        const unsigned c = c0 + r;
-        const bool active = c < fan;
+        const bool active = c0 + r < fan;
+        const unsigned c = child_bits(S, meta, c0 + r);
         bool keep = false, cand = false;
         if (active) {
             if (use_tv) {

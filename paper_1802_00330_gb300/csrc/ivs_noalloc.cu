@@ -219,7 +219,8 @@ extern "C" int ivs_solve_noalloc(const ivs_system *s, const double *box_lo, cons
     if (o->centred_form && m != n)
         return err(IVS_ERR_INVALID, "ivs_solve_noalloc: the centred form needs n_eqs == n_vars");
     if (!(o->tol >= 0) || !std::isfinite(o->tol) || o->hs_iters < 0 || o->max_depth < 0 || o->max_depth > 0xFFF0 ||
-        o->root_depth < 0 || o->root_depth > o->max_depth)
+        o->root_depth < 0 || o->root_depth > o->max_depth || o->split_mode < 0 || o->split_mode > 1 ||
+        o->gap_split < 0 || o->gap_split > 1)
         return err(IVS_ERR_INVALID, "ivs_solve_noalloc: bad options");
 
     DevSys d{};
@@ -239,6 +240,8 @@ extern "C" int ivs_solve_noalloc(const ivs_system *s, const double *box_lo, cons
     d.max_boxes = o->max_boxes;
     d.centred = o->centred_form ? 1 : 0;
     d.krawczyk = o->krawczyk ? 1 : 0;
+    d.bisect = o->split_mode == 1 ? 1 : 0;
+    d.gap_split = o->gap_split ? 1 : 0;
 
     // ---- set-up, once per device (with that device current) ----
     int dev = 0;
@@ -377,6 +380,7 @@ extern "C" int ivs_solve_noalloc(const ivs_system *s, const double *box_lo, cons
         stats->excluded_prefilter = (int64_t)hs[ST_EXCL_PREFILTER];
         stats->excluded_eval = (int64_t)hs[ST_EXCL_EVAL];
         stats->excluded_centred = (int64_t)hs[ST_EXCL_CENTRED];
+        stats->gap_splits = (int64_t)hs[ST_GAP_SPLITS];
         stats->hs_applied = (int64_t)hs[ST_HS_APPLIED];
         stats->hs_empty = (int64_t)hs[ST_HS_EMPTY];
         stats->hs_contracted = (int64_t)hs[ST_HS_CONTRACTED];

@@ -412,6 +412,7 @@ int ivs_server::step(std::vector<std::pair<uint64_t, ivs_result *>> &finished) {
             st.excluded_prefilter = (int64_t)v[ST_EXCL_PREFILTER];
             st.excluded_eval = (int64_t)v[ST_EXCL_EVAL];
             st.excluded_centred = (int64_t)v[ST_EXCL_CENTRED];
+            st.gap_splits = (int64_t)v[ST_GAP_SPLITS];
             st.hs_applied = (int64_t)v[ST_HS_APPLIED];
             st.hs_empty = (int64_t)v[ST_HS_EMPTY];
             st.hs_contracted = (int64_t)v[ST_HS_CONTRACTED];
@@ -507,6 +508,7 @@ int ivs_server_create(const ivs_server_cfg *cfg, ivs_server **out) {
         if (cfg->max_vars > 0) c.max_vars = cfg->max_vars;
         if (cfg->sweeps_per_step > 0) c.sweeps_per_step = cfg->sweeps_per_step;
         if (cfg->reserve_factor > 0) c.reserve_factor = cfg->reserve_factor;
+        if (cfg->min_region_entries > 0) c.min_region_entries = cfg->min_region_entries;
         c.device = cfg->device;
     }
     if (c.max_vars > kMaxVars || c.max_slots > 65536 || c.wave_children < ((int64_t)1 << c.max_vars))
@@ -537,7 +539,9 @@ int ivs_server_submit(ivs_server *sv, const ivs_system *s, const double *box_lo,
     rq.lo.assign(box_lo, box_lo + s->n_vars);
     rq.hi.assign(box_hi, box_hi + s->n_vars);
     rq.opt = *opt;
-    rq.reserve = std::max<int64_t>((int64_t)(64.0 * sv->cfg.reserve_factor * (double)((int64_t)1 << s->n_vars)),
+    rq.reserve = std::max<int64_t>(std::max<int64_t>((int64_t)(64.0 * sv->cfg.reserve_factor *
+                                                                 (double)((int64_t)1 << s->n_vars)),
+                                                       sv->cfg.min_region_entries),
                                    ((int64_t)1 << s->n_vars) + 1);
     rq.t_submit = Clock::now();
     {
