@@ -315,6 +315,25 @@ int ivs_clusters(int32_t n_vars, int64_t count, const double *lo, const double *
 int ivs_backtrack(int32_t n_vars, int64_t count, const double *lo, const double *hi, const double *box_lo,
                   const double *box_hi, int32_t level, int64_t max_cells, int64_t *n_cells, int64_t *n_groups);
 
+/* The same two operations on the GPU (Section 3.4, Algorithm 5), with the same results:
+ * ivs_clusters_gpu and ivs_backtrack_gpu take host rows like the functions above (copied
+ * to device `device`, scratch allocated per call); ivs_plan_clusters and
+ * ivs_plan_backtrack work on a plan's device-resident result of system s after
+ * ivs_plan_run, with that system's initial box, on the plan's stream -- no host copy of
+ * the boxes.  Cells are sorted on the device as 128-bit keys (coordinate 0 most
+ * significant), so the GPU backtracking needs n_vars * level <= 127 (IVS_ERR_INVALID
+ * beyond); groups and clusters come from a union-find over the candidate pairs that a
+ * binary search over the sorted keys leaves (IVS_ERR_BUDGET above 4e9 pairs; as above,
+ * above max_cells cells).  ivs_plan_clusters returns the count only. */
+int ivs_clusters_gpu(int32_t n_vars, int64_t count, const double *lo, const double *hi, int64_t *n_clusters,
+                     int64_t *label, double *cl_lo, double *cl_hi, int64_t cl_cap, int32_t device);
+int ivs_backtrack_gpu(int32_t n_vars, int64_t count, const double *lo, const double *hi, const double *box_lo,
+                      const double *box_hi, int32_t level, int64_t max_cells, int64_t *n_cells, int64_t *n_groups,
+                      int32_t device);
+int ivs_plan_backtrack(ivs_plan *p, int32_t s, int32_t level, int64_t max_cells, int64_t *n_cells,
+                       int64_t *n_groups);
+int ivs_plan_clusters(ivs_plan *p, int32_t s, int64_t *n_clusters);
+
 /* ---- allocation-free solve ------------------------------------------------------ */
 /* No counterpart in the paper: an entry point for callers that cannot allocate.
  * Processes whose device memory belongs to a pool they must not bypass (a framework's

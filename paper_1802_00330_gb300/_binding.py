@@ -76,6 +76,13 @@ SIGNATURES = {
     "ivs_clusters": (C.c_int, [C.c_int32, C.c_int64, _VP, _VP, C.POINTER(C.c_int64), _VP, _VP, _VP, C.c_int64]),
     "ivs_backtrack": (C.c_int, [C.c_int32, C.c_int64, _VP, _VP, _VP, _VP, C.c_int32, C.c_int64,
                                 C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "ivs_clusters_gpu": (C.c_int, [C.c_int32, C.c_int64, _VP, _VP, C.POINTER(C.c_int64), _VP, _VP, _VP, C.c_int64,
+                                   C.c_int32]),
+    "ivs_backtrack_gpu": (C.c_int, [C.c_int32, C.c_int64, _VP, _VP, _VP, _VP, C.c_int32, C.c_int64,
+                                    C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int32]),
+    "ivs_plan_backtrack": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int64, C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_int64)]),
+    "ivs_plan_clusters": (C.c_int, [_VP, C.c_int32, C.POINTER(C.c_int64)]),
     "ivs_solve": (C.c_int, [C.POINTER(ivs_system), _VP, _VP, C.POINTER(ivs_options), _PP]),
     "ivs_solve_batch": (C.c_int, [C.c_int32, C.POINTER(ivs_system), _VP, _VP, C.POINTER(ivs_options),
                                   C.c_int32, _PP]),
@@ -278,6 +285,20 @@ class Plan:
         finally:
             self._lib.ivs_result_free(res)
 
+    def backtrack(self, s, level, max_cells=1 << 26):
+        """Algorithm 5 on the GPU over system s's device-resident result: (distinct cells of
+        the level, connected groups of them) -- ``ivs_plan_backtrack``."""
+        cells, groups = C.c_int64(), C.c_int64()
+        _check(self._lib.ivs_plan_backtrack(self.p, int(s), int(level), int(max_cells), C.byref(cells),
+                                            C.byref(groups)))
+        return cells.value, groups.value
+
+    def clusters(self, s):
+        """Connected components of touching boxes of system s's result, on the GPU."""
+        nc = C.c_int64()
+        _check(self._lib.ivs_plan_clusters(self.p, int(s), C.byref(nc)))
+        return nc.value
+
     def kernel_times(self):
         arr = (ivs_kernel_time * 64)()
         k = self._lib.ivs_plan_kernel_times(self.p, arr, 64)
@@ -428,6 +449,38 @@ def clusters(lo, hi, with_hulls=True):
                             _ptr(hl) if with_hulls else None, _ptr(hh) if with_hulls else None, k))
     c = nc.value
     return c, labels[:k], hl[:c], hh[:c]
+
+
+def clusters_gpu(lo, hi, device=0):
+    """``ivs_clusters`` on the GPU (``ivs_clusters_gpu``): (count, labels, hull_lo, hull_hi)."""
+    lib = load()
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    k = lo.shape[0]
+    n = lo.shape[1] if lo.ndim == 2 and k else 1
+    nc = C.c_int64()
+    labels = np.zeros(max(k, 1), np.int64)
+    hl = np.zeros((max(k, 1), n))
+    hh = np.zeros((max(k, 1), n))
+    _check(lib.ivs_clusters_gpu(n, k, _ptr(lo), _ptr(hi), C.byref(nc), _ptr(labels), _ptr(hl), _ptr(hh), k,
+                                int(device)))
+    c = nc.value
+    return c, labels[:k], hl[:c], hh[:c]
+
+
+def backtrack_gpu(lo, hi, box_lo, box_hi, level, max_cells=1 << 26, groups=False, device=0):
+    """``ivs_backtrack`` on the GPU (``ivs_backtrack_gpu``)."""
+    lib = load()
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    bl = np.ascontiguousarray(box_lo, dtype=np.float64)
+    bh = np.ascontiguousarray(box_hi, dtype=np.float64)
+    k = lo.shape[0]
+    out = C.c_int64()
+    grp = C.c_int64()
+    _check(lib.ivs_backtrack_gpu(len(bl), k, _ptr(lo), _ptr(hi), _ptr(bl), _ptr(bh), int(level), int(max_cells),
+                                 C.byref(out), C.byref(grp), int(device)))
+    return (out.value, grp.value) if groups else out.value
 
 
 def backtrack(lo, hi, box_lo, box_hi, level, max_cells=1 << 26, groups=False):

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libivsolve.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
-SOURCES = ["ivs_kernels.cu", "ivs_host.cu", "ivs_hostcore.cu", "ivs_server.cu", "ivs_probe.cu", "ivs_noalloc.cu", "ivs_clusters.cu", "ivs_hs_1.cu", "ivs_hs_2.cu", "ivs_hs_3.cu", "ivs_hs_4.cu"]
+SOURCES = ["ivs_kernels.cu", "ivs_host.cu", "ivs_hostcore.cu", "ivs_server.cu", "ivs_probe.cu", "ivs_noalloc.cu", "ivs_clusters.cu", "ivs_roots.cu", "ivs_hs_1.cu", "ivs_hs_2.cu", "ivs_hs_3.cu", "ivs_hs_4.cu"]
 HEADERS = ["ivs_internal.h", "ivs_interval.cuh", "ivs_kernels.cuh", "ivs_hs.cuh", "ivs_tab.cuh", "ivs_hostcore.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-ftz=false", "-prec-div=true",

@@ -76,6 +76,7 @@ struct ivs_plan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     int64_t *h_wave_limit = nullptr;       // pinned
+    std::vector<double> box_lo_h, box_hi_h;   // initial boxes, n_max per system
 };
 
 
@@ -187,6 +188,11 @@ int plan_create_impl(int32_t n_sys, const ivs_system *systems, const double *con
             p->time_budget_s = p->time_budget_s > 0 ? std::min(p->time_budget_s, o->time_budget_s) : o->time_budget_s;
     }
     std::sort(p->dims.begin(), p->dims.end());
+    for (int s = 0; s < n_sys; s++)
+        for (int j = 0; j < p->n_max; j++) {
+            p->box_lo_h.push_back(j < systems[s].n_vars ? box_lo[s][j] : 0.0);
+            p->box_hi_h.push_back(j < systems[s].n_vars ? box_hi[s][j] : 0.0);
+        }
     for (int s = 0; s < n_sys; s++) {
         for (int j = 0; j < p->n_max; j++) {
             bool in = j < systems[s].n_vars;
@@ -494,6 +500,28 @@ static void fill_stats(const ivs_plan *p, int s, ivs_stats *st) {
     st->device_ms = p->last_ms;
     st->launches = p->launches;
 }
+
+}  // extern "C"
+
+// The device-resident result region of system s after the last run (for the GPU root
+// isolation in ivs_roots.cu): coordinate j of box i at lo[i + j * stride].
+int plan_result_view(ivs_plan *p, int32_t s, const double **lo, const double **hi, int64_t *count, int64_t *stride,
+                     int *n, const double **box_lo, const double **box_hi, cudaStream_t *st, int *device) {
+    if (!p || s < 0 || s >= p->n_sys) return fail(IVS_ERR_INVALID, "bad plan or system index");
+    const unsigned long long *sv = p->h_stats.data() + (size_t)s * ST_COUNT;
+    *count = std::min<int64_t>((int64_t)sv[ST_OUT], p->sys_out_cap[s]);
+    *lo = p->args.out.lo + p->sys_out_base[s];
+    *hi = p->args.out.hi + p->sys_out_base[s];
+    *stride = p->args.out.cap;
+    *n = p->sys_n[s];
+    *box_lo = p->box_lo_h.data() + (size_t)s * p->n_max;
+    *box_hi = p->box_hi_h.data() + (size_t)s * p->n_max;
+    *st = p->stream;
+    *device = p->device;
+    return IVS_OK;
+}
+
+extern "C" {
 
 int ivs_plan_stats(ivs_plan *p, ivs_stats *st) {
     if (!p || !st) return fail(IVS_ERR_INVALID, "null argument");
