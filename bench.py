@@ -14,7 +14,7 @@ roofline of every kernel class, the serial oracle on the host cores, and the sin
 solve as a sub-object.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W]
-                  [--workload batched|n6|n2|n10|paper|served] [--impl ivsolve|reference]
+                  [--workload batched|n6|n2|n10|paper|paper_tables|served] [--impl ivsolve|reference]
 """
 
 from __future__ import annotations
@@ -697,6 +697,80 @@ def serve_stream(B, systems, times, budget, max_slots, workspace_gib, min_region
     return results, lat, wall, st
 
 
+# the paper's printed per-round counts (Section 4): B&B boxes kept per round (Tables 1, 4,
+# 7), Hansen-Sengupta origin -> new boxes per round (Tables 2, 5) and the backtracking
+# boxes per width (Tables 3, 6, 8; width -> count)
+PAPER_ROUNDS = {"katsura8": [1, 511, 4847, 92880, 2549461, 76736464, 794760638, 430650061],
+                "noon9": [1, 512, 5120, 42176, 13511, 222941, 1156044, 11471246, 33925040, 28775053],
+                "kinema": [1, 288, 5714, 56036, 407380, 4369735, 26247657, 87424465]}
+PAPER_HS = {"katsura8": (8, [(430650061, 4900601), (30098623, 4347544), (42617540, 5532835), (64267381, 7946423),
+                             (105056246, 11571157), (165616092, 15474734), (243760141, 18711270),
+                             (295102270, 20306174), (343840882, 20242072)]),
+            "noon9": (10, [(28775053, 477)])}
+PAPER_BACKTRACK = {"noon9": {0.03125: 477, 0.0625: 19, 0.125: 19},
+                   "kinema": {0.001953125: 6587702, 0.00390625: 328906, 0.0078125: 14876, 0.015625: 453,
+                              0.03125: 8, 0.0625: 8}}
+
+
+def run_paper_tables(args, rank, local_rank):
+    """The paper's Section 4 tables beside this solver's counts on the same printed
+    systems: B&B rounds without contraction (Tables 1, 4, 7), the Hansen-Sengupta rounds
+    from the round the paper starts it (Tables 2, 5), and the backtracking boxes and
+    isolated roots per width after a solve to tol 1e-3 with HS from the first round
+    (Tables 6, 8).  Counts come from the per-depth counters of one run each."""
+    import dataclasses
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_1802_00330_gb300 import _binding as B
+    if rank != 0:
+        return
+    fx = {k: synth.load_fixture(os.path.join(ROOT, "tests", "golden", f"{k}.txt")) for k in PAPER_ROUNDS}
+    out = {"metric": "per-round box counts against the paper's Section 4 tables", "config": {
+        "workload": "the paper's printed systems katsura8 ([-1,1]^9), noon9 ([-8,8]^9), kinema ([-32,32]^9)"}}
+    bb = {}
+    for name, want in PAPER_ROUNDS.items():
+        t = time.perf_counter()
+        r = B.solve(fx[name], hs_enable=0, tol=0.0, max_depth=len(want) - 1, max_results=1 << 16)
+        got = r["stats"]["depth_kept"][: len(want)].tolist()
+        bb[name] = {"rounds": list(range(1, len(want) + 1)), "ours": got, "paper": want,
+                    "equal": [a == b for a, b in zip(got, want)], "seconds": time.perf_counter() - t}
+    out["bb_rounds"] = bb
+    hs = {}
+    for name, (first, rows) in PAPER_HS.items():
+        t = time.perf_counter()
+        last = first - 1 + len(rows) - 1   # depth of the last printed round
+        r = B.solve(fx[name], hs_min_depth=first - 1, tol=0.0, max_depth=last, max_results=1 << 16)
+        st = r["stats"]
+        ours = [(int(st["depth_hs"][d]), int(st["depth_kept"][d])) for d in range(first - 1, last + 1)]
+        hs[name] = {"rounds": list(range(first, first + len(rows))), "ours_origin_new": ours, "paper_origin_new": rows,
+                    "ours_new_fraction": [n / o if o else None for o, n in ours],
+                    "paper_new_fraction": [n / o for o, n in rows], "seconds": time.perf_counter() - t}
+    out["hs_rounds"] = hs
+    bt = {}
+    for name, widths in PAPER_BACKTRACK.items():
+        s = dataclasses.replace(fx[name], tol=1e-3)
+        plan = B.Plan([s])
+        try:
+            plan.run()
+            rows = []
+            for w, want in widths.items():
+                level = int(round(np.log2((s.box_hi[0] - s.box_lo[0]) / w)))
+                if s.n_vars * level <= 127:
+                    cells, groups = plan.backtrack(0, level)
+                    where = "gpu"
+                else:   # beyond the device keys' 127 bits: the host routine on the same boxes
+                    r = plan.result(0)
+                    cells, groups = B.backtrack(r["lo"], r["hi"], s.box_lo, s.box_hi, level, groups=True)
+                    where = "host"
+                rows.append({"width": w, "level": level, "ours_cells": cells, "ours_groups": groups,
+                             "paper_boxes": want, "computed_on": where})
+        finally:
+            plan.close()
+        bt[name] = rows
+    out["backtracking"] = bt
+    print(json.dumps(out), flush=True)
+
+
 def run_served(args, rank, world, local_rank):
     """Continuous batching: a Poisson stream of served-recipe systems, submitted at their
     arrival times to one server.  First the stream at a low rate, which labels the
@@ -803,6 +877,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.workload == "served" and args.impl != "reference":
         run_served(args, rank, world, local_rank)
+        return
+    if args.workload == "paper_tables":
+        run_paper_tables(args, rank, local_rank)
         return
     if args.workload == "served":
         systems = synth.served_systems(64)

@@ -171,6 +171,13 @@ int ivs_result_status(const ivs_result *r);
  * int32 each; any of them may be NULL. */
 int ivs_result_boxes(const ivs_result *r, double *lo, double *hi, int32_t *flags, int32_t *depth);
 int ivs_result_stats(const ivs_result *r, ivs_stats *st);
+/* Per depth d = 0..63 (depths above 63 counted in slot 63): boxes processed at depth d;
+ * boxes that survived the evaluation (and the contraction, when applied) there; boxes
+ * that entered the contraction there.  With a split at every depth these are the
+ * paper's boxes per round (round d + 1, Tables 1, 4, 7) and, with hs_min_depth, its
+ * Hansen-Sengupta "origin" (entered) and "new" (survived) boxes (Tables 2, 5).  Each
+ * array holds 64 int64; any may be NULL. */
+int ivs_result_depth_stats(const ivs_result *r, int64_t *boxes, int64_t *kept, int64_t *entered_hs);
 void ivs_result_free(ivs_result *r);
 
 /* ---- device-resident plan: upload once, solve many times ---------------------- */

@@ -91,6 +91,7 @@ SIGNATURES = {
     "ivs_result_status": (C.c_int, [_VP]),
     "ivs_result_boxes": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "ivs_result_stats": (C.c_int, [_VP, C.POINTER(ivs_stats)]),
+    "ivs_result_depth_stats": (C.c_int, [_VP, _VP, _VP, _VP]),
     "ivs_result_free": (None, [_VP]),
     "ivs_workspace_bytes": (C.c_size_t, [C.c_int32, C.POINTER(ivs_system), C.c_int64, C.c_int64, C.c_int64]),
     "ivs_plan_create": (C.c_int, [C.c_int32, C.POINTER(ivs_system), _VP, _VP, C.POINTER(ivs_options),
@@ -208,8 +209,16 @@ def result_to_dict(r):
     _check(lib.ivs_result_boxes(r, _ptr(lo), _ptr(hi), _ptr(flags), _ptr(depth)))
     st = ivs_stats()
     _check(lib.ivs_result_stats(r, C.byref(st)))
+    stats = {k: getattr(st, k) for k, _ in ivs_stats._fields_}
+    db = np.zeros(64, np.int64)
+    dk = np.zeros(64, np.int64)
+    dh = np.zeros(64, np.int64)
+    _check(lib.ivs_result_depth_stats(r, _ptr(db), _ptr(dk), _ptr(dh)))
+    stats["depth_boxes"] = db
+    stats["depth_kept"] = dk
+    stats["depth_hs"] = dh
     return {"status": lib.ivs_result_status(r), "lo": lo, "hi": hi, "flags": flags, "depth": depth,
-            "stats": {k: getattr(st, k) for k, _ in ivs_stats._fields_}}
+            "stats": stats}
 
 
 def solve(s, box_lo=None, box_hi=None, **opts):

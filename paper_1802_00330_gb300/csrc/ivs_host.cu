@@ -75,6 +75,7 @@ struct ivs_plan {
     bool use_graph = true;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    int graph_kernels = 0;                 // kernels per sweep of the graph body
     int64_t *h_wave_limit = nullptr;       // pinned
     std::vector<double> box_lo_h, box_hi_h;   // initial boxes, n_max per system
 };
@@ -340,9 +341,10 @@ int plan_create_impl(int32_t n_sys, const ivs_system *systems, const double *con
             r->eval_threads == p->eval_threads && r->num_sms == p->num_sms) {
             std::swap(p->graph, r->graph);          // same kernels, same arguments: same graph
             std::swap(p->graph_exec, r->graph_exec);
+            p->graph_kernels = r->graph_kernels;
         } else {
             CUDA_TRY(build_sweep_graph(a, p->dims.data(), (int)p->dims.size(), p->eval_blocks, p->eval_threads,
-                                       p->num_sms, &p->graph));
+                                       p->num_sms, &p->graph, &p->graph_kernels));
             CUDA_TRY(cudaGraphInstantiate(&p->graph_exec, p->graph, 0));
         }
     }
@@ -422,7 +424,7 @@ int ivs_plan_run(ivs_plan *p) {
             CUDA_TRY(cudaMemcpyAsync(p->h_stats.data(), a.stats, p->h_stats.size() * sizeof(unsigned long long),
                                      cudaMemcpyDeviceToHost, st));
             CUDA_TRY(cudaStreamSynchronize(st));
-            p->launches += (5 + nd) * (p->h_ctl->waves - waves_done);
+            p->launches += (int64_t)p->graph_kernels * (p->h_ctl->waves - waves_done);
             waves_done = p->h_ctl->waves;
             if (p->h_ctl->error) { status = IVS_ERR_NOMEM; break; }
             if (p->h_ctl->top == 0) break;
@@ -433,9 +435,10 @@ int ivs_plan_run(ivs_plan *p) {
         }
     } else {
         for (;;) {
+            int kernels = 0;
             CUDA_TRY(launch_sweep(a, p->dims.data(), nd, p->eval_blocks, p->eval_threads, p->num_sms, st,
-                                  p->profile ? p->stage_ev.data() : nullptr));
-            p->launches += 4 + nd;
+                                  p->profile ? p->stage_ev.data() : nullptr, &kernels));
+            p->launches += kernels;
             CUDA_TRY(cudaMemcpyAsync(p->h_ctl, a.ctl, sizeof(WaveCtl), cudaMemcpyDeviceToHost, st));
             CUDA_TRY(cudaStreamSynchronize(st));
             if (p->profile) {
@@ -556,6 +559,11 @@ int ivs_plan_result(ivs_plan *p, int32_t s, ivs_result **out) {
     r->n = n;
     fill_sorted(r.get(), n, total, lo, hi, flags, depth);
     fill_stats(p, s, &r->st);
+    for (int q = 0; q < kDepthSlots; q++) {
+        r->depth_boxes[q] = (int64_t)sv[ST_DEPTH_BOXES + q];
+        r->depth_kept[q] = (int64_t)sv[ST_DEPTH_KEPT + q];
+        r->depth_hs[q] = (int64_t)sv[ST_DEPTH_HS + q];
+    }
     const unsigned long long fl = p->h_stats[(size_t)s * ST_COUNT + ST_FLAGS];
     int status = p->run_status;
     if (status == IVS_OK && fl) status = IVS_ERR_BUDGET;
@@ -644,6 +652,13 @@ int ivs_result_boxes(const ivs_result *r, double *lo, double *hi, int32_t *flags
     if (hi && !r->hi.empty()) std::memcpy(hi, r->hi.data(), r->hi.size() * 8);
     if (flags && !r->flags.empty()) std::memcpy(flags, r->flags.data(), r->flags.size() * 4);
     if (depth && !r->depth.empty()) std::memcpy(depth, r->depth.data(), r->depth.size() * 4);
+    return IVS_OK;
+}
+int ivs_result_depth_stats(const ivs_result *r, int64_t *boxes, int64_t *kept, int64_t *entered_hs) {
+    if (!r) return fail(IVS_ERR_INVALID, "null result");
+    if (boxes) std::memcpy(boxes, r->depth_boxes, sizeof(r->depth_boxes));
+    if (kept) std::memcpy(kept, r->depth_kept, sizeof(r->depth_kept));
+    if (entered_hs) std::memcpy(entered_hs, r->depth_hs, sizeof(r->depth_hs));
     return IVS_OK;
 }
 int ivs_result_stats(const ivs_result *r, ivs_stats *st) {

@@ -17,6 +17,8 @@ struct ivs_result {
     std::vector<double> lo, hi;          // row-major, sorted, -0 written as +0
     std::vector<int32_t> flags, depth;
     ivs_stats st{};
+    int64_t depth_boxes[64] = {}, depth_kept[64] = {};   // per depth (the last slot: >= 63)
+    int64_t depth_hs[64] = {};                             // boxes entering the contraction
 };
 
 namespace ivs {

@@ -36,7 +36,7 @@ namespace cg = cooperative_groups;
 
 namespace hsd {
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kCS = 4;          // CTAs per cluster in the cooperative form
+constexpr int kCS = 4;          // CTAs per cluster in the cooperative form (8 measured no faster)
 constexpr int kCoopMaxN = 12;   // the cooperative form exists for n <= 12
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
@@ -71,7 +71,10 @@ struct Cfg {
     static constexpr int BB = (N >= 15) ? 16 : 32;   // boxes per chunk
     static constexpr int NW = (N <= 3) ? 4 : 8;      // warps per block
     static constexpr int NT = NW * 32;
-    static constexpr int MIN_BLOCKS = (N <= 10) ? 2 : 1;
+    // blocks per SM: three for n = 7, 8 (80 registers, a few bytes of spill; measured 3-4%
+    // faster on the batch's wide sweeps than two at 128 registers; the narrow n = 6 sweeps
+    // measured 2% slower with three), two up to n = 10, then one
+    static constexpr int MIN_BLOCKS = (N == 7 || N == 8) ? 3 : (N <= 10) ? 2 : 1;
     // doubles
     static constexpr int XLO = 0;                    // N rows: box lo
     static constexpr int XHI = XLO + N * BB;         // N: box hi
@@ -641,6 +644,8 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
                 const bool run = si[C::I_HS + b] && !si[C::I_CEX + b];
                 si[C::I_RUN + b] = run ? (a.tb.sys[si[C::I_SYS + b]].krawczyk ? 2 : 1) : 0;
                 st_app += run ? 1u : 0u;
+                if (run && it == 0 && rank == 0)   // every CTA of a cluster runs this; one counts
+                    atomicAdd(stat_ptr(a, sys, ST_DEPTH_HS + (depth < kDepthSlots ? depth : kDepthSlots - 1)), 1ull);
                 if (si[C::I_CEX + b]) {
                     dropped_c = true;
                     stopped = true;
@@ -811,6 +816,8 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
             // statistics (new parents also enter the live count): one atomic per warp when
             // the warp holds a single system; the sweep's counters only in the first pass
             const bool p0 = pass == 0;
+            if (p0 && fate != 0)   // survived evaluation and contraction at its depth
+                atomicAdd(stat_ptr(a, sys, ST_DEPTH_KEPT + (depth < kDepthSlots ? depth : kDepthSlots - 1)), 1ull);
             unsigned v[10] = {p0 ? st_app : 0u, st_empty, p0 ? st_con : 0u, p0 ? st_sing : 0u,
                               (fate == 1 && flag != 4) ? 1u : 0u, st_uns, fate == 2 ? 1u : 0u, fate == 2 ? 1u : 0u,
                               st_cex, p0 ? st_gap : 0u};
@@ -858,7 +865,8 @@ constexpr size_t kOneCtaPerSm = 120 * 1024;
 int coop_clusters_cached(const void *func, int num_sms, int threads, size_t smem, cudaError_t *err);
 
 template <int N>
-static cudaError_t launch_hs_n(const SweepArgs &a, int num_sms, cudaStream_t st) {
+static cudaError_t launch_hs_n(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels) {
+    *kernels = 1;
     using C = hsd::Cfg<N>;
     // cache the term table in shared memory when the plan holds one system and it fits
     const bool cache = a.single && (size_t)a.blob_smem + C::BYTES <= kHsSmemLimit;
@@ -878,6 +886,7 @@ static cudaError_t launch_hs_n(const SweepArgs &a, int num_sms, cudaStream_t st)
             k_hs_coop<N><<<active_clusters * hsd::kCS, C::NT, csmem, st>>>(a, cache ? 1 : 0, coop_max);
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
+            *kernels = 2;
         }
       }
     }

@@ -3,8 +3,8 @@
 
 namespace ivs {
 
-cudaError_t launch_hs_dim14(const SweepArgs &a, int num_sms, cudaStream_t st) { return launch_hs_n<14>(a, num_sms, st); }
-cudaError_t launch_hs_dim15(const SweepArgs &a, int num_sms, cudaStream_t st) { return launch_hs_n<15>(a, num_sms, st); }
-cudaError_t launch_hs_dim16(const SweepArgs &a, int num_sms, cudaStream_t st) { return launch_hs_n<16>(a, num_sms, st); }
+cudaError_t launch_hs_dim14(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels) { return launch_hs_n<14>(a, num_sms, st, kernels); }
+cudaError_t launch_hs_dim15(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels) { return launch_hs_n<15>(a, num_sms, st, kernels); }
+cudaError_t launch_hs_dim16(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels) { return launch_hs_n<16>(a, num_sms, st, kernels); }
 
 }  // namespace ivs

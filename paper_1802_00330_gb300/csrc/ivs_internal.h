@@ -39,8 +39,13 @@ enum Stat : int {
     ST_LIVE,           // queue entries of the system (0 after a sweep: the system is solved)
     ST_EXCL_CENTRED,   // boxes the centred form dropped
     ST_GAP_SPLITS,     // sweeps that returned two boxes at an extended-division gap
-    ST_COUNT
+    ST_DEPTH_BOXES,    // kDepthSlots slots: boxes processed at depth d (d >= 63 in the last)
+    ST_DEPTH_KEPT = ST_DEPTH_BOXES + 64,   // 64 slots: boxes that survived evaluation and
+                                           // contraction at depth d
+    ST_DEPTH_HS = ST_DEPTH_KEPT + 64,      // 64 slots: boxes that entered the contraction
+    ST_COUNT = ST_DEPTH_HS + 64
 };
+constexpr int kDepthSlots = 64;
 constexpr int64_t kFlagResultOverflow = 1, kFlagDepthCut = 2, kFlagBudget = 4;
 
 // Compiled system, resident on the device.  Its polynomials (the m equations F_i, then

@@ -247,9 +247,17 @@ __global__ void __launch_bounds__(kBeginThreads) k_wave_begin(SweepArgs a) {
     c->waves += 1;
 }
 
-__global__ void k_commit(SweepArgs a, int n_max) {
+// Moves the sweep's new parents onto the queue.  In the sweep graph (use_cond) block 0
+// also sets the WHILE condition: more sweeps while the queue is non-empty after this
+// commit, no error occurred and the sweep limit is not reached (nothing after the commit
+// changes any of them).
+__global__ void k_commit(SweepArgs a, int n_max, cudaGraphConditionalHandle h, int use_cond) {
     const WaveCtl *c = a.ctl;
     const int64_t staged = c->staged, base = c->base;
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) {
+        const bool more = base + staged > 0 && c->error == 0 && c->waves < c->wave_limit;
+        cudaGraphSetConditional(h, more ? 1u : 0u);
+    }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < staged; i += stride) {
         int64_t d = base + i;
@@ -332,13 +340,6 @@ __global__ void k_cancel_regions(SweepArgs a, const int32_t *cancel) {
         a.rg.rem[sl] = 0;
         a.rg.cursor[sl] = 0;
     }
-}
-
-__global__ void k_loop_cond(SweepArgs a, cudaGraphConditionalHandle h) {
-    if (threadIdx.x != 0) return;
-    const WaveCtl *c = a.ctl;
-    const bool more = c->top > 0 && c->error == 0 && c->waves < c->wave_limit;
-    cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // ------------------------------------------------------------------------------------
@@ -530,6 +531,8 @@ __device__ __forceinline__ void eval_parent(const SweepArgs &a, WaveCtl *ctl, co
         if (r == 0) {
             atomicAdd(stat_ptr(a, sys, ST_BOXES), (unsigned long long)fan);
             atomicMax(stat_ptr(a, sys, ST_MAX_DEPTH), (unsigned long long)depth);
+            atomicAdd(stat_ptr(a, sys, ST_DEPTH_BOXES + (depth < kDepthSlots ? depth : kDepthSlots - 1)),
+                      (unsigned long long)fan);
         }
         if (cnt_pre) atomicAdd(stat_ptr(a, sys, ST_EXCL_PREFILTER), (unsigned long long)cnt_pre);
         if (cnt_ev) atomicAdd(stat_ptr(a, sys, ST_EXCL_EVAL), (unsigned long long)cnt_ev);
@@ -647,24 +650,24 @@ __global__ void __launch_bounds__(kEval64Threads) k_eval64(SweepArgs a) {
 // launchers
 // ------------------------------------------------------------------------------------
 
-static cudaError_t launch_hs(const SweepArgs &a, int n, int num_sms, cudaStream_t st) {
+static cudaError_t launch_hs(const SweepArgs &a, int n, int num_sms, cudaStream_t st, int *kernels) {
     switch (n) {
-    case 1: return launch_hs_dim1(a, num_sms, st);
-    case 2: return launch_hs_dim2(a, num_sms, st);
-    case 3: return launch_hs_dim3(a, num_sms, st);
-    case 4: return launch_hs_dim4(a, num_sms, st);
-    case 5: return launch_hs_dim5(a, num_sms, st);
-    case 6: return launch_hs_dim6(a, num_sms, st);
-    case 7: return launch_hs_dim7(a, num_sms, st);
-    case 8: return launch_hs_dim8(a, num_sms, st);
-    case 9: return launch_hs_dim9(a, num_sms, st);
-    case 10: return launch_hs_dim10(a, num_sms, st);
-    case 11: return launch_hs_dim11(a, num_sms, st);
-    case 12: return launch_hs_dim12(a, num_sms, st);
-    case 13: return launch_hs_dim13(a, num_sms, st);
-    case 14: return launch_hs_dim14(a, num_sms, st);
-    case 15: return launch_hs_dim15(a, num_sms, st);
-    case 16: return launch_hs_dim16(a, num_sms, st);
+    case 1: return launch_hs_dim1(a, num_sms, st, kernels);
+    case 2: return launch_hs_dim2(a, num_sms, st, kernels);
+    case 3: return launch_hs_dim3(a, num_sms, st, kernels);
+    case 4: return launch_hs_dim4(a, num_sms, st, kernels);
+    case 5: return launch_hs_dim5(a, num_sms, st, kernels);
+    case 6: return launch_hs_dim6(a, num_sms, st, kernels);
+    case 7: return launch_hs_dim7(a, num_sms, st, kernels);
+    case 8: return launch_hs_dim8(a, num_sms, st, kernels);
+    case 9: return launch_hs_dim9(a, num_sms, st, kernels);
+    case 10: return launch_hs_dim10(a, num_sms, st, kernels);
+    case 11: return launch_hs_dim11(a, num_sms, st, kernels);
+    case 12: return launch_hs_dim12(a, num_sms, st, kernels);
+    case 13: return launch_hs_dim13(a, num_sms, st, kernels);
+    case 14: return launch_hs_dim14(a, num_sms, st, kernels);
+    case 15: return launch_hs_dim15(a, num_sms, st, kernels);
+    case 16: return launch_hs_dim16(a, num_sms, st, kernels);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -726,11 +729,12 @@ cudaError_t configure_eval_kernels(const SweepArgs &a) {
     return allow_max_dynamic_smem((const void *)k_eval64);
 }
 
-cudaError_t launch_sweep(const SweepArgs &a, const int *hs_dims, int n_hs_dims, int eval_blocks,
-                         int eval_threads, int num_sms, cudaStream_t st, cudaEvent_t *ev) {
+static cudaError_t launch_sweep_impl(const SweepArgs &a, const int *hs_dims, int n_hs_dims, int eval_blocks,
+                                     int num_sms, cudaStream_t st, cudaEvent_t *ev, cudaGraphConditionalHandle h,
+                                     int use_cond, int *kernels) {
+    int count = 4;   // wave_begin, eval, eval64, commit
     // ev (optional): n_hs_dims + 5 events recorded between the stages
     const size_t blob = a.single ? (size_t)a.blob_smem : 0;
-    (void)eval_threads;
     if (ev) cudaEventRecord(ev[0], st);
     k_wave_begin<<<1, kBeginThreads, 0, st>>>(a);
     if (ev) cudaEventRecord(ev[1], st);
@@ -739,17 +743,27 @@ cudaError_t launch_sweep(const SweepArgs &a, const int *hs_dims, int n_hs_dims, 
     k_eval64<<<num_sms * 4, kEval64Threads, blob, st>>>(a);
     if (ev) cudaEventRecord(ev[3], st);
     for (int q = 0; q < n_hs_dims; q++) {
-        cudaError_t e = launch_hs(a, hs_dims[q], num_sms, st);
+        int kq = 0;
+        cudaError_t e = launch_hs(a, hs_dims[q], num_sms, st, &kq);
         if (e != cudaSuccess) return e;
+        count += kq;
         if (ev) cudaEventRecord(ev[4 + q], st);
     }
-    k_commit<<<num_sms * 4, 256, 0, st>>>(a, a.max_fan_shift);
+    k_commit<<<num_sms * 4, 256, 0, st>>>(a, a.max_fan_shift, h, use_cond);
     if (ev) cudaEventRecord(ev[4 + n_hs_dims], st);
+    if (kernels) *kernels = count;
     return cudaGetLastError();
 }
 
+cudaError_t launch_sweep(const SweepArgs &a, const int *hs_dims, int n_hs_dims, int eval_blocks,
+                         int eval_threads, int num_sms, cudaStream_t st, cudaEvent_t *ev, int *kernels) {
+    (void)eval_threads;
+    return launch_sweep_impl(a, hs_dims, n_hs_dims, eval_blocks, num_sms, st, ev, cudaGraphConditionalHandle{}, 0,
+                             kernels);
+}
+
 cudaError_t build_sweep_graph(const SweepArgs &a, const int *hs_dims, int n_hs_dims, int eval_blocks,
-                              int eval_threads, int num_sms, cudaGraph_t *out) {
+                              int eval_threads, int num_sms, cudaGraph_t *out, int *kernels_per_sweep) {
     *out = nullptr;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaGraphCreate(&g, 0);
@@ -769,8 +783,9 @@ cudaError_t build_sweep_graph(const SweepArgs &a, const int *hs_dims, int n_hs_d
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t le = launch_sweep(a, hs_dims, n_hs_dims, eval_blocks, eval_threads, num_sms, cs, nullptr);
-            k_loop_cond<<<1, 32, 0, cs>>>(a, h);
+            (void)eval_threads;
+            cudaError_t le = launch_sweep_impl(a, hs_dims, n_hs_dims, eval_blocks, num_sms, cs, nullptr, h, 1,
+                                               kernels_per_sweep);
             cudaGraph_t captured = nullptr;
             e = cudaStreamEndCapture(cs, &captured);
             if (e == cudaSuccess && le != cudaSuccess) e = le;

@@ -53,14 +53,15 @@ inline void choose_eval_layout(SweepArgs &a, int max_tv) {
     a.eval_warps = warps;
     a.tv_stride = ((size_t)max_tv * 16 <= budget) ? max_tv : 0;
 }
-// kernels per sweep: 4 + n_hs_dims; ev (nullable) receives n_hs_dims + 4 stage events
+// one sweep; ev (nullable) receives n_hs_dims + 5 stage events; *kernels (nullable) the
+// number of kernels launched
 cudaError_t launch_sweep(const SweepArgs &a, const int *hs_dims, int n_hs_dims, int eval_blocks,
-                         int eval_threads, int num_sms, cudaStream_t st, cudaEvent_t *ev);
-// The sweep loop as one CUDA graph: a conditional WHILE node whose body is one sweep
-// followed by a kernel that keeps the condition set while the queue is non-empty, no
-// error occurred and ctl->waves < ctl->wave_limit.  Kernels per iteration: 5 + n_hs_dims.
+                         int eval_threads, int num_sms, cudaStream_t st, cudaEvent_t *ev, int *kernels = nullptr);
+// The sweep loop as one CUDA graph: a conditional WHILE node whose body is one sweep; its
+// commit kernel keeps the condition set while the queue is non-empty, no error occurred
+// and ctl->waves < ctl->wave_limit.  Kernels per iteration: 4 + n_hs_dims.
 cudaError_t build_sweep_graph(const SweepArgs &a, const int *hs_dims, int n_hs_dims, int eval_blocks,
-                              int eval_threads, int num_sms, cudaGraph_t *out);
+                              int eval_threads, int num_sms, cudaGraph_t *out, int *kernels_per_sweep = nullptr);
 // directed-rounding rate microbenchmark (kind 0 FP64, 1 FP32); returns ops and fills ms
 cudaError_t run_probe(int kind, int num_sms, double *ops, float *ms);
 cudaError_t launch_seed_roots(const SweepArgs &a, const double *d_box_lo, const double *d_box_hi,
@@ -72,22 +73,23 @@ cudaError_t launch_cancel_regions(const SweepArgs &a, const int32_t *d_cancel, c
 // the start of each system's region
 cudaError_t launch_admit(const SweepArgs &a, const double *d_lo, const double *d_hi, const int32_t *d_slot,
                          const int32_t *d_depth, int count, int n_max, cudaStream_t st);
-// Hansen-Sengupta + accept/split kernel for dimension n (ivs_hs_*.cu)
-cudaError_t launch_hs_dim1(const SweepArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_hs_dim2(const SweepArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_hs_dim3(const SweepArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_hs_dim4(const SweepArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_hs_dim5(const SweepArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_hs_dim6(const SweepArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_hs_dim7(const SweepArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_hs_dim8(const SweepArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_hs_dim9(const SweepArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_hs_dim10(const SweepArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_hs_dim11(const SweepArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_hs_dim12(const SweepArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_hs_dim13(const SweepArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_hs_dim14(const SweepArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_hs_dim15(const SweepArgs &a, int num_sms, cudaStream_t st);
-cudaError_t launch_hs_dim16(const SweepArgs &a, int num_sms, cudaStream_t st);
+// Hansen-Sengupta + accept/split kernels for dimension n (ivs_hs_*.cu); *kernels receives
+// how many kernels the call launched (1, or 2 with the cooperative form)
+cudaError_t launch_hs_dim1(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels);
+cudaError_t launch_hs_dim2(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels);
+cudaError_t launch_hs_dim3(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels);
+cudaError_t launch_hs_dim4(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels);
+cudaError_t launch_hs_dim5(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels);
+cudaError_t launch_hs_dim6(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels);
+cudaError_t launch_hs_dim7(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels);
+cudaError_t launch_hs_dim8(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels);
+cudaError_t launch_hs_dim9(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels);
+cudaError_t launch_hs_dim10(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels);
+cudaError_t launch_hs_dim11(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels);
+cudaError_t launch_hs_dim12(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels);
+cudaError_t launch_hs_dim13(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels);
+cudaError_t launch_hs_dim14(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels);
+cudaError_t launch_hs_dim15(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels);
+cudaError_t launch_hs_dim16(const SweepArgs &a, int num_sms, cudaStream_t st, int *kernels);
 
 }  // namespace ivs

@@ -413,6 +413,11 @@ int ivs_server::step(std::vector<std::pair<uint64_t, ivs_result *>> &finished) {
             st.excluded_eval = (int64_t)v[ST_EXCL_EVAL];
             st.excluded_centred = (int64_t)v[ST_EXCL_CENTRED];
             st.gap_splits = (int64_t)v[ST_GAP_SPLITS];
+            for (int q = 0; q < kDepthSlots; q++) {
+                r->depth_boxes[q] = (int64_t)v[ST_DEPTH_BOXES + q];
+                r->depth_kept[q] = (int64_t)v[ST_DEPTH_KEPT + q];
+                r->depth_hs[q] = (int64_t)v[ST_DEPTH_HS + q];
+            }
             st.hs_applied = (int64_t)v[ST_HS_APPLIED];
             st.hs_empty = (int64_t)v[ST_HS_EMPTY];
             st.hs_contracted = (int64_t)v[ST_HS_CONTRACTED];

@@ -120,6 +120,8 @@ def assert_same(g, o):
     for k in ("hs_applied", "hs_empty", "hs_contracted", "hs_singular", "accepted", "unsplittable", "split",
               "excluded_centred", "max_depth_seen"):
         assert gs[k] == os_[k], k
+    assert np.array_equal(gs["depth_boxes"], os_["depth_boxes"])
+    assert np.array_equal(gs["depth_kept"], os_["depth_kept"])
 
 
 def _gpu_kw(case, method, **extra):
