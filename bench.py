@@ -118,9 +118,15 @@ def hs_ops(s, krawczyk=False):
 # workload, valid only for the kernel sources it was taken with: the bench reports null
 # once their hash (code without comments and whitespace) differs.  Each record names the
 # capture it came from (profiles/).
+# A record gives bytes per launch, or bytes per Hansen-Sengupta box (taken on a smaller
+# case of the same kernel and scaled to a launch of the measured step by its own boxes per
+# launch: the traffic grows with the boxes a launch processes).
 TRAFFIC = {
     ("n6", "hs_n6"): {"sources_sha256": "62891eeae8663b1de6d2d8d6266de4e64e29152cb3868fb6bbab36a76f7ec840",
                       "bytes_per_launch": 485350, "default_options_only": True},
+    # profiles/k_hs_n8_batched.md: 13.02 GB over 112,757,665 n = 8 boxes of all launches
+    ("batched", "hs_n8"): {"sources_sha256": "d2e66d7d4971a3118ca76bb77801e1102fc39b081d466a1d5fb5e977a9d66458",
+                           "bytes_per_hs_box": 115.45, "default_options_only": True},
 }
 KERNEL_SOURCES = ("ivs_hs.cuh", "ivs_tab.cuh", "ivs_interval.cuh", "ivs_internal.h", "ivs_kernels.cuh")
 
@@ -147,14 +153,18 @@ def hs_sources_sha(read=None, files=KERNEL_SOURCES):
     return h.hexdigest()
 
 
-def traffic_of(workload_name, kernel, default_options=True):
+def traffic_of(workload_name, kernel, default_options=True, hs_boxes_per_launch=None):
     rec = TRAFFIC.get((workload_name, kernel))
     if rec is None or (rec.get("default_options_only") and not default_options):
         return None
     files = rec.get("files", KERNEL_SOURCES)
     if rec["sources_sha256"] != hs_sources_sha(files=files):
         return None
-    return rec["bytes_per_launch"]
+    if "bytes_per_launch" in rec:
+        return rec["bytes_per_launch"]
+    if hs_boxes_per_launch is None:
+        return None
+    return rec["bytes_per_hs_box"] * hs_boxes_per_launch
 
 
 # ---- multi-rank aggregation ----------------------------------------------------------
@@ -368,11 +378,12 @@ def class_rooflines(B, prof, systems, krawczyk, fp64_rate, fp32_rate, ktimes, st
     time, against the measured directed rate of its pipe.  hs_n<k>: hs_ops of every sweep
     run on the systems of size k; eval (FP32 stage): one natural-form evaluation per
     child; eval64: one FP64 evaluation per undecided child."""
-    per = [prof.result(k)["stats"] for k in range(len(systems))]
-    ops = {}
+    per = [prof.result_stats(k) for k in range(len(systems))]
+    ops, hs_boxes = {}, {}
     for s, st in zip(systems, per):
         key = f"hs_n{s.n_vars}"
         ops[key] = ops.get(key, 0.0) + st["hs_applied"] * hs_ops(s, krawczyk)
+        hs_boxes[key] = hs_boxes.get(key, 0) + int(st["depth_hs"].sum())
         ops["eval"] = ops.get("eval", 0.0) + st["boxes"] * eval_ops(s)
         ops["eval64"] = ops.get("eval64", 0.0) + st["eval64_boxes"] * eval_ops(s)
     total_ms = sum(v[1] for v in ktimes.values())
@@ -386,6 +397,8 @@ def class_rooflines(B, prof, systems, krawczyk, fp64_rate, fp32_rate, ktimes, st
                   "frac": ach / (peak / 1e12), "kernel_share": ms / total_ms,
                   "avg_launch_ms": ms / max(1, launches), "launches": launches,
                   "pipe": "fp32" if k == "eval" else "fp64"}
+        if k in hs_boxes:
+            out[k]["hs_boxes_per_launch"] = hs_boxes[k] * steps / max(1, launches)
     return out
 
 
@@ -590,7 +603,8 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
     dom = max(classes.values(), key=lambda v: v["kernel_share"])
     roofline = dict(dom)
     roofline.update({
-        "traffic": traffic_of(args.workload, dom["kernel"], not (args.centred or args.krawczyk)),
+        "traffic": traffic_of(args.workload, dom["kernel"], not (args.centred or args.krawczyk),
+                              dom.get("hs_boxes_per_launch")),
         "op_convention": "one directed add or multiply = 1 flop (no FMA on the path)",
         "peak_source": f"measured in this run: directed {'__fadd_rd/__fmul_ru' if dom['pipe'] == 'fp32' else '__dadd_rd/__dmul_ru'} probe",
         "work": ("natural-form operations per child through the FP32 stage" if dom["kernel"] == "eval" else
@@ -707,6 +721,8 @@ PAPER_HS = {"katsura8": (8, [(430650061, 4900601), (30098623, 4347544), (4261754
                              (105056246, 11571157), (165616092, 15474734), (243760141, 18711270),
                              (295102270, 20306174), (343840882, 20242072)]),
             "noon9": (10, [(28775053, 477)])}
+# Table 3 (katsura8 after the Hansen-Sengupta rounds up to 16), its coarser widths
+PAPER_BACKTRACK_KATSURA8 = {0.0078125: 2957, 0.015625: 691, 0.03125: 246, 0.0625: 79, 0.125: 36, 0.25: 36}
 PAPER_BACKTRACK = {"noon9": {0.03125: 477, 0.0625: 19, 0.125: 19},
                    "kinema": {0.001953125: 6587702, 0.00390625: 328906, 0.0078125: 14876, 0.015625: 453,
                               0.03125: 8, 0.0625: 8}}
@@ -739,12 +755,27 @@ def run_paper_tables(args, rank, local_rank):
     for name, (first, rows) in PAPER_HS.items():
         t = time.perf_counter()
         last = first - 1 + len(rows) - 1   # depth of the last printed round
-        r = B.solve(fx[name], hs_min_depth=first - 1, tol=0.0, max_depth=last, max_results=1 << 16)
-        st = r["stats"]
-        ours = [(int(st["depth_hs"][d]), int(st["depth_kept"][d])) for d in range(first - 1, last + 1)]
-        hs[name] = {"rounds": list(range(first, first + len(rows))), "ours_origin_new": ours, "paper_origin_new": rows,
-                    "ours_new_fraction": [n / o if o else None for o, n in ours],
-                    "paper_new_fraction": [n / o for o, n in rows], "seconds": time.perf_counter() - t}
+        # the last round's boxes stay on the device for Table 3's backtracking
+        plan = B.Plan([fx[name]], opts={"hs_min_depth": first - 1, "tol": 0.0, "max_depth": last,
+                                        "max_results": 1 << 26})
+        try:
+            plan.run()
+            st = plan.result_stats(0)
+            ours = [(int(st["depth_hs"][d]), int(st["depth_kept"][d])) for d in range(first - 1, last + 1)]
+            hs[name] = {"rounds": list(range(first, first + len(rows))), "ours_origin_new": ours,
+                        "paper_origin_new": rows, "ours_new_fraction": [n / o if o else None for o, n in ours],
+                        "paper_new_fraction": [n / o for o, n in rows], "seconds": time.perf_counter() - t}
+            if name == "katsura8":
+                s = fx[name]
+                rows3 = []
+                for w, want in PAPER_BACKTRACK_KATSURA8.items():
+                    level = int(round(np.log2((s.box_hi[0] - s.box_lo[0]) / w)))
+                    cells, groups = plan.backtrack(0, level, max_cells=1 << 30)
+                    rows3.append({"width": w, "level": level, "ours_cells": cells, "ours_groups": groups,
+                                  "paper_boxes": want})
+                out["backtracking_katsura8"] = {"boxes_backtracked": ours[-1][1], "rows": rows3}
+        finally:
+            plan.close()
     out["hs_rounds"] = hs
     bt = {}
     for name, widths in PAPER_BACKTRACK.items():
@@ -864,7 +895,7 @@ def main():
     ap.add_argument("--served-budget", type=float, default=1.0)
     ap.add_argument("--served-slots", type=int, default=256)
     ap.add_argument("--served-workspace", type=int, default=96, help="GiB")
-    ap.add_argument("--served-min-region", type=int, default=1 << 18,
+    ap.add_argument("--served-min-region", type=int, default=1 << 21,
                     help="smallest queue region of a request (entries)")
     ap.add_argument("--batched-count", type=int, default=4096)
     ap.add_argument("--centred", action="store_true",

@@ -209,6 +209,9 @@ int ivs_plan_run(ivs_plan *p);
 /* Copies system s's result of the last run to the host. */
 int ivs_plan_result(ivs_plan *p, int32_t s, ivs_result **out);
 int ivs_plan_stats(ivs_plan *p, ivs_stats *st);   /* totals over all systems, last run */
+/* System s's counters of the last run and its per-depth counts (as ivs_result_depth_stats)
+ * without copying its boxes; any output may be NULL. */
+int ivs_plan_depth_stats(ivs_plan *p, int32_t s, ivs_stats *st, int64_t *boxes, int64_t *kept, int64_t *entered_hs);
 void ivs_plan_destroy(ivs_plan *p);
 
 /* Autotuner of the batching form (no paper counterpart): for the given systems it runs

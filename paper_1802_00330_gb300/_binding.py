@@ -99,6 +99,7 @@ SIGNATURES = {
     "ivs_plan_run": (C.c_int, [_VP]),
     "ivs_plan_result": (C.c_int, [_VP, C.c_int32, _PP]),
     "ivs_plan_stats": (C.c_int, [_VP, C.POINTER(ivs_stats)]),
+    "ivs_plan_depth_stats": (C.c_int, [_VP, C.c_int32, C.POINTER(ivs_stats), _VP, _VP, _VP]),
     "ivs_plan_destroy": (None, [_VP]),
     "ivs_plan_kernel_times": (C.c_int32, [_VP, _VP, C.c_int32]),
     "ivs_autotune": (C.c_int, [C.c_int32, C.POINTER(ivs_system), _VP, _VP, C.POINTER(ivs_options), C.c_int32,
@@ -307,6 +308,16 @@ class Plan:
         nc = C.c_int64()
         _check(self._lib.ivs_plan_clusters(self.p, int(s), C.byref(nc)))
         return nc.value
+
+    def result_stats(self, s=0):
+        """Counters of system s's last run (with the per-depth counts) without copying its
+        boxes to the host."""
+        st = ivs_stats()
+        db, dk, dh = (np.zeros(64, np.int64) for _ in range(3))
+        _check(self._lib.ivs_plan_depth_stats(self.p, int(s), C.byref(st), _ptr(db), _ptr(dk), _ptr(dh)))
+        out = {k: getattr(st, k) for k, _ in ivs_stats._fields_}
+        out.update(depth_boxes=db, depth_kept=dk, depth_hs=dh)
+        return out
 
     def kernel_times(self):
         arr = (ivs_kernel_time * 64)()

@@ -526,6 +526,21 @@ int plan_result_view(ivs_plan *p, int32_t s, const double **lo, const double **h
 
 extern "C" {
 
+int ivs_plan_depth_stats(ivs_plan *p, int32_t s, ivs_stats *st, int64_t *boxes, int64_t *kept, int64_t *entered_hs) {
+    if (!p || s < 0 || s >= p->n_sys) return fail(IVS_ERR_INVALID, "bad arguments");
+    const unsigned long long *v = p->h_stats.data() + (size_t)s * ST_COUNT;
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        fill_stats(p, s, st);
+    }
+    for (int q = 0; q < kDepthSlots; q++) {
+        if (boxes) boxes[q] = (int64_t)v[ST_DEPTH_BOXES + q];
+        if (kept) kept[q] = (int64_t)v[ST_DEPTH_KEPT + q];
+        if (entered_hs) entered_hs[q] = (int64_t)v[ST_DEPTH_HS + q];
+    }
+    return IVS_OK;
+}
+
 int ivs_plan_stats(ivs_plan *p, ivs_stats *st) {
     if (!p || !st) return fail(IVS_ERR_INVALID, "null argument");
     std::memset(st, 0, sizeof(*st));

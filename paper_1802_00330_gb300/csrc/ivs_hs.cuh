@@ -616,10 +616,11 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
             si[C::I_SYS + b] = sys;
             si[C::I_ITS + b] = its > cen ? its : cen;   // passes: the centred test needs J, f once
         }
-        __syncthreads();
-        int max_it = 0;
-        for (int b = 0; b < BB; b++) max_it = max(max_it, si[C::I_ITS + b]);
-        for (int it = 0; it < max_it; it++) {
+        // passes while some box wants one (a block-wide vote; in the cooperative form every
+        // CTA holds the same boxes, so all of them take the same number of passes)
+        const int my_passes = owner ? (its > cen ? its : cen) : 0;
+        int my_cen = 0, my_kr = 0;   // this owner's box takes the centred test / Krawczyk step
+        for (int it = 0; __syncthreads_or(my_passes > it); it++) {
             // pass `it`: J(X), f(x); on the first pass the centred test (if asked), then
             // the Hansen-Sengupta sweep for the boxes that want one and were not excluded
             if (owner) {
@@ -627,7 +628,8 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
                 const bool jf = active && !stopped && it < si[C::I_ITS + b];
                 si[C::I_JF + b] = jf ? 1 : 0;
                 si[C::I_HS + b] = (jf && it < its) ? 1 : 0;
-                si[C::I_CEN + b] = (jf && it == 0 && cen) ? 1 : 0;
+                my_cen = (jf && it == 0 && cen) ? 1 : 0;
+                si[C::I_CEN + b] = my_cen;
                 si[C::I_CEX + b] = 0;
                 si[C::I_BAD + b] = 0;
                 si[C::I_EMPTY + b] = 0;
@@ -636,13 +638,12 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
             }
             __syncthreads();
             jf_block<N, COOP>(a, blob_smem, sd, si, t);
-            int any_cen = 0;
-            for (int b = 0; b < BB; b++) any_cen |= si[C::I_CEN + b];
-            if (any_cen) centred_block<N>(sd, si, t);
+            if (__syncthreads_or(my_cen)) centred_block<N>(sd, si, t);
             if (owner) {
                 const int b = t;
                 const bool run = si[C::I_HS + b] && !si[C::I_CEX + b];
                 si[C::I_RUN + b] = run ? (a.tb.sys[si[C::I_SYS + b]].krawczyk ? 2 : 1) : 0;
+                my_kr = si[C::I_RUN + b] == 2 ? 1 : 0;
                 st_app += run ? 1u : 0u;
                 if (run && it == 0 && rank == 0)   // every CTA of a cluster runs this; one counts
                     atomicAdd(stat_ptr(a, sys, ST_DEPTH_HS + (depth < kDepthSlots ? depth : kDepthSlots - 1)), 1ull);
@@ -660,9 +661,7 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
             gj_block<N>(sd, si, t);
             m_block<N, COOP>(sd, si, t);
             gs_block<N>(sd, si, t, gr);
-            int any_kr = 0;
-            for (int b = 0; b < BB; b++) any_kr |= si[C::I_RUN + b] == 2;
-            if (any_kr) kr_block<N>(sd, si, t);
+            if (__syncthreads_or(my_kr)) kr_block<N>(sd, si, t);
             if (owner && si[C::I_RUN + t]) {
                 const int b = t;
                 if (si[C::I_EMPTY + b]) {
@@ -807,7 +806,8 @@ __device__ __forceinline__ void hs_body(const SweepArgs &a, int cache_blob, int6
                             a.stage.hi[j * a.stage.cap + k] = hi;
                         }
                         a.stage.sys[k] = sys;
-                        a.stage.meta[k] = ((uint32_t)depth & kDepthMask) | (bis ? ((uint32_t)jw << kSplitShift) : 0u);
+                        a.stage.meta[k] = ((uint32_t)depth & kDepthMask) | (bis ? ((uint32_t)jw << kSplitShift) : 0u) |
+                                          ((uint32_t)(bis ? 1 : N) << kFanShift);
                     } else {
                         ctl->error = 1;
                     }

@@ -18,6 +18,10 @@ constexpr uint32_t kDepthMask = 0xFFFFu;
 // `coordinate` of c) reads [lo_j, hi_j] there whatever the decoding.
 constexpr int kSplitShift = 16;
 constexpr uint32_t kSplitMask = 0xFu;
+// log2 of a parent's number of children (n, or 1 when bisected), bits 20-24 of its meta
+// word, so the sweep's pop can size parents from the meta word alone
+constexpr int kFanShift = 20;
+constexpr uint32_t kFanMask = 0x1Fu;
 
 // per-system statistics slots (int64 counters on the device)
 enum Stat : int {
@@ -140,6 +144,7 @@ struct DevRegions {
     int64_t *prefix;                 // [n + 1]
     unsigned long long *cursor;
     int32_t n;
+    int32_t fair_share;              // 1: rotating fair share instead of least served first
 };
 
 // survivor of the evaluation: parent index in the queue, child index

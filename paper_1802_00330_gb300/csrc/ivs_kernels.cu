@@ -39,11 +39,18 @@ __device__ __forceinline__ unsigned long long *stat_ptr(const SweepArgs &a, int 
 // top - K + children <= cap.  One block scans the fan-outs of the top entries.
 constexpr int kBeginThreads = 1024;
 constexpr int kBeginPer = 64;       // entries per thread: a window of 65536 parents
-// Serving with per-system regions: every region with entries gets a fair share of the
-// sweep's W children (at least one parent), limited by what its region can hold in the
-// worst case; slots are served in an order that rotates with the sweep count, and once W
-// is used up the remaining slots wait for the next sweep.  One block.
-__device__ void wave_begin_regions(const SweepArgs &a) {
+constexpr size_t kBeginSmem = (size_t)kBeginThreads * kBeginPer;   // one byte per window entry
+// Serving with per-system regions, one block.  Least attained service first (the
+// default): the regions with entries are taken in order of the boxes their request has
+// processed so far (fewest first; a bitonic sort of up to kLasMax slots in shared memory),
+// and each pops as many parents as its region allows until the sweep's W children are
+// used up -- requests that need little work finish in few sweeps, whatever else is in
+// flight.  Fair share (rg.fair_share, or more than kLasMax slots): every region gets W
+// divided by the regions with entries (at least one parent), in an order that rotates
+// with the sweep count.  Either way a region pops breadth first while under half full
+// and one parent at a time beyond; the schedule never changes a result.
+constexpr int kLasMax = 4096;
+__device__ void wave_begin_regions(const SweepArgs &a, unsigned long long *s_key) {
     __shared__ long long s_red[kBeginThreads];
     __shared__ long long s_active, s_total, s_run;
     const DevRegions &rg = a.rg;
@@ -64,15 +71,45 @@ __device__ void wave_begin_regions(const SweepArgs &a) {
     atomicAdd((unsigned long long *)&s_active, (unsigned long long)act);
     atomicAdd((unsigned long long *)&s_total, (unsigned long long)tot);
     __syncthreads();
-    const long long share = a.wave_children / (s_active > 0 ? s_active : 1);
-    // rotated order: position q serves slot (q + waves) % S; chunks of kBeginThreads slots
-    // are scanned in order with a running total of children
+    const bool las = !rg.fair_share && S <= kLasMax;
+    const long long share = las ? a.wave_children : a.wave_children / (s_active > 0 ? s_active : 1);
+    if (las) {
+        // keys (boxes processed, slot), slots without entries last; sorted ascending
+        int n2 = 1;
+        while (n2 < S) n2 <<= 1;
+        for (int q = t; q < n2; q += kBeginThreads) {
+            unsigned long long key = ~0ull;
+            if (q < S) {
+                const unsigned long long done = a.stats[(size_t)q * ST_COUNT + ST_BOXES];
+                const unsigned long long cap = 1ull << 40;
+                key = ((rg.rem[q] > 0 ? (done < cap ? done : cap) : 2 * cap) << 13) | (unsigned long long)q;
+            }
+            s_key[q] = key;
+        }
+        __syncthreads();
+        for (int kk = 2; kk <= n2; kk <<= 1)
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                for (int q = t; q < n2; q += kBeginThreads) {
+                    const int l = q ^ j;
+                    if (l > q) {
+                        const unsigned long long x = s_key[q], y = s_key[l];
+                        if (((q & kk) == 0) ? (y < x) : (x < y)) {
+                            s_key[q] = y;
+                            s_key[l] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+    }
+    // position q serves slot order[q] (least served first) or (q + waves) % S (rotating);
+    // chunks of kBeginThreads positions are scanned in order with a running total of children
     for (int q0 = 0; q0 < S; q0 += kBeginThreads) {
         const int q = q0 + t;
         long long want = 0, fan = 1, k = 0;
         int sl = -1;
         if (q < S) {
-            sl = (int)(((int64_t)q + waves) % S);
+            sl = las ? (int)(s_key[q] & 8191ull) : (int)(((int64_t)q + waves) % S);
             const int64_t held = rg.rem[sl];
             if (held > 0) {
                 const bool root = held == 1 && (a.q.meta[rg.base[sl]] & kRootFlag) != 0;
@@ -153,10 +190,12 @@ __device__ __forceinline__ int64_t parent_index(const SweepArgs &a, int64_t base
 }
 
 __global__ void __launch_bounds__(kBeginThreads) k_wave_begin(SweepArgs a) {
+    // log2 children of the window's entries; serving: the sort keys of the slots
+    extern __shared__ __align__(8) unsigned char s_fan[];
     __shared__ long long s_sum[kBeginThreads];
     __shared__ long long s_first;
     if (a.rg.n > 0) {
-        wave_begin_regions(a);
+        wave_begin_regions(a, reinterpret_cast<unsigned long long *>(s_fan));
         return;
     }
     WaveCtl *c = a.ctl;
@@ -193,11 +232,17 @@ __global__ void __launch_bounds__(kBeginThreads) k_wave_begin(SweepArgs a) {
         return;
     }
     const int64_t window = top < (int64_t)kBeginThreads * kBeginPer ? top : (int64_t)kBeginThreads * kBeginPer;
-    // entry i (0-based from the top) is queue index top - 1 - i
-    auto fan_of = [&](int64_t i) -> long long {
-        const int64_t e = top - 1 - i;
-        return fan_out(a.tb.sys[a.q.sys[e]], a.q.meta[e]);
-    };
+    // entry i (0-based from the top) is queue index top - 1 - i; its log2 children come
+    // from its meta word (0 for an initial box), read once with coalesced loads
+    for (int q = 0; q < kBeginPer; q++) {
+        const int64_t i = (int64_t)q * kBeginThreads + t;
+        if (i < window) {
+            const uint32_t m = a.q.meta[top - 1 - i];
+            s_fan[i] = (m & kRootFlag) ? 0 : (unsigned char)((m >> kFanShift) & kFanMask);
+        }
+    }
+    __syncthreads();
+    auto fan_of = [&](int64_t i) -> long long { return 1ll << s_fan[i]; };
     long long local = 0;
     for (int q = 0; q < kBeginPer; q++) {
         const int64_t i = (int64_t)t * kBeginPer + q;
@@ -547,7 +592,7 @@ __device__ __forceinline__ void eval_parent(const SweepArgs &a, WaveCtl *ctl, co
 // gives each block its parents and spreads a parent's table entries and children over
 // all of the block's threads, so the few parents of the first and last sweeps finish
 // sooner.  Both run the same per-child arithmetic.
-__global__ void __launch_bounds__(kEvalThreads) k_eval(SweepArgs a) {
+__global__ void __launch_bounds__(kEvalThreads, 3) k_eval(SweepArgs a) {
     extern __shared__ __align__(16) char s_blob[];
     float4 *s_tv_base = reinterpret_cast<float4 *>(s_blob + (a.single ? a.blob_smem : 0));
     __shared__ double s_p[kEvalWarps][3][kMaxVars];
@@ -724,7 +769,9 @@ cudaError_t allow_max_dynamic_smem(const void *func) {
 
 cudaError_t configure_eval_kernels(const SweepArgs &a) {
     (void)a;
-    cudaError_t e = allow_max_dynamic_smem((const void *)k_eval);
+    cudaError_t e = allow_max_dynamic_smem((const void *)k_wave_begin);
+    if (e != cudaSuccess) return e;
+    e = allow_max_dynamic_smem((const void *)k_eval);
     if (e != cudaSuccess) return e;
     return allow_max_dynamic_smem((const void *)k_eval64);
 }
@@ -736,7 +783,7 @@ static cudaError_t launch_sweep_impl(const SweepArgs &a, const int *hs_dims, int
     // ev (optional): n_hs_dims + 5 events recorded between the stages
     const size_t blob = a.single ? (size_t)a.blob_smem : 0;
     if (ev) cudaEventRecord(ev[0], st);
-    k_wave_begin<<<1, kBeginThreads, 0, st>>>(a);
+    k_wave_begin<<<1, kBeginThreads, kBeginSmem, st>>>(a);
     if (ev) cudaEventRecord(ev[1], st);
     k_eval<<<eval_blocks, a.eval_warps * 32, eval_smem_bytes(a), st>>>(a);
     if (ev) cudaEventRecord(ev[2], st);
