@@ -238,9 +238,11 @@ int32_t ivs_plan_kernel_times(ivs_plan *p, ivs_kernel_time *out, int32_t max);
  * counterpart; it supplies the roofline denominator): kind 0 = FP64 (__dadd_rd /
  * __dmul_ru chains), kind 1 = FP32 (__fadd_rd / __fmul_ru), kind 2 / 3 = FP64 with only
  * 8 / 1 lanes of each warp active (counts only active-lane operations: shows whether
- * idle lanes cost FP64 issue time).  Writes the rate in operations per second (one add
- * or one multiply = one operation) and the kernel time. */
+ * idle lanes cost FP64 issue time), kind 4 / 5 = FP64 division, directed (__ddiv_rd /
+ * __ddiv_ru) / round to nearest.  Writes the rate in operations per second (one add,
+ * multiply or division = one operation) and the kernel time. */
 int ivs_probe_rate(int32_t kind, int32_t device, double *ops_per_s, double *ms);
+
 
 /* ---- serving: continuous batching over one shared device queue ------------------- */
 /* A server keeps one device-resident queue for every system in flight.  Requests that
@@ -248,8 +250,12 @@ int ivs_probe_rate(int32_t kind, int32_t device, double *ops_per_s, double *ms);
  * evaluation of every child of the popped parents, then Algorithm 3 and the accept /
  * split step) as soon as a slot and queue memory are free: each request owns a region of
  * 64 * 2^n queue entries (reserve_factor scales it; at least min_region_entries), and
- * requests wait, in arrival order, until one is free.  Every sweep gives each request in flight a fair share of its
- * children, and their sweeps share kernels.  A system is solved when none of its
+ * requests wait, in arrival order, until one is free.  Each sweep's children go to the
+ * requests in flight in order of the boxes each has processed so far, fewest first (least
+ * attained service: a request that needs little work finishes in few sweeps whatever
+ * else is in flight; up to 4096 slots), or, with schedule = 1, in equal shares in an order
+ * that rotates every sweep; a request whose region is more than half full takes one
+ * parent per sweep.  Their sweeps share kernels; the schedule never changes a result.  A system is solved when none of its
  * boxes remain in the queue; its result (the same as ivs_solve's, bit for bit: each box's
  * fate depends only on the box) is then ready for ivs_server_poll / ivs_server_wait.
  * A request whose options set time_budget_s > 0 and that is still unsolved that long
@@ -272,6 +278,7 @@ typedef struct ivs_server_cfg {
                                  minimum beyond 64 * 2^n): a region that is more than half
                                  full gives its request one parent per sweep, so a larger
                                  region lets small requests finish in fewer sweeps        */
+    int32_t schedule;         /* 0: least attained service first; 1: rotating equal shares */
 } ivs_server_cfg;
 
 typedef struct ivs_server_stats {

@@ -54,7 +54,8 @@ class ivs_plan_cfg(C.Structure):
 class ivs_server_cfg(C.Structure):
     _fields_ = [("workspace_bytes", C.c_size_t), ("wave_children", C.c_int64), ("results_per_slot", C.c_int64),
                 ("max_slots", C.c_int32), ("max_vars", C.c_int32), ("sweeps_per_step", C.c_int32),
-                ("device", C.c_int32), ("reserve_factor", C.c_double), ("min_region_entries", C.c_int64)]
+                ("device", C.c_int32), ("reserve_factor", C.c_double), ("min_region_entries", C.c_int64),
+                ("schedule", C.c_int32)]
 
 
 class ivs_server_stats(C.Structure):
@@ -337,7 +338,8 @@ class Plan:
 
 
 def probe_rate(kind=0, device=0):
-    """Measured directed-rounding rate of the device in ops/s (kind 0 FP64, 1 FP32)."""
+    """Measured directed-rounding rate of the device in ops/s (kind 0 FP64, 1 FP32, 2 / 3
+    FP64 with 8 / 1 active lanes, 4 / 5 FP64 division directed / to nearest)."""
     ops = C.c_double()
     ms = C.c_double()
     _check(load().ivs_probe_rate(int(kind), int(device), C.byref(ops), C.byref(ms)))
@@ -349,7 +351,7 @@ class Server:
     poll or wait for their results."""
 
     def __init__(self, workspace_bytes=0, wave_children=0, results_per_slot=0, max_slots=0, max_vars=0,
-                 sweeps_per_step=0, device=0, reserve_factor=0.0, min_region_entries=0):
+                 sweeps_per_step=0, device=0, reserve_factor=0.0, min_region_entries=0, schedule=0):
         lib = load()
         self._lib = lib
         cfg = ivs_server_cfg()
@@ -357,7 +359,7 @@ class Server:
         for k, v in (("workspace_bytes", workspace_bytes), ("wave_children", wave_children),
                      ("results_per_slot", results_per_slot), ("max_slots", max_slots), ("max_vars", max_vars),
                      ("sweeps_per_step", sweeps_per_step), ("reserve_factor", reserve_factor),
-                     ("min_region_entries", min_region_entries)):
+                     ("min_region_entries", min_region_entries), ("schedule", schedule)):
             if v:
                 setattr(cfg, k, v)
         cfg.device = int(device)

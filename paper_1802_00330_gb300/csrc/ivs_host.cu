@@ -646,7 +646,7 @@ int32_t ivs_plan_kernel_times(ivs_plan *p, ivs_kernel_time *out, int32_t max) {
 }
 
 int ivs_probe_rate(int32_t kind, int32_t device, double *ops_per_s, double *ms) {
-    if (!ops_per_s || kind < 0 || kind > 3) return fail(IVS_ERR_INVALID, "bad arguments");
+    if (!ops_per_s || kind < 0 || kind > 5) return fail(IVS_ERR_INVALID, "bad arguments");
     CUDA_TRY(cudaSetDevice(device));
     int sms = 0;
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));

@@ -388,18 +388,34 @@ struct GapRec {
     double w, llo, lhi, ulo, uhi;
 };
 
+// warps 0 and 1 alone (the two threads of a box in the Gauss-Seidel rows)
+__device__ __forceinline__ void pair_sync() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
+
 // Gauss-Seidel (eq 21-22).  Row i folds r_i and the products M_ij (Y_j - x_j), j != i,
-// in order j = 1..n; products with j > i use the box's own coordinates and are formed
-// up front, those with j < i as soon as Y_j is final.  A product is written over M_ij,
-// which nothing reads afterwards.  With gr.on (the owner's box asks for the two-box
+// in order j = 1..n, into s_i; then Y_i = X_i meets x_i - s_i / M_ii (extended division).
+// Work split:
+// * the products with j > i use the box's own coordinates: formed up front, one (i, j)
+//   pair per unit, and written over M_ij (nothing reads M_ij afterwards);
+// * the terms with j < i join s_i as soon as Y_j is final: while row j's owners work on
+//   row j + 1, the other warps add term j to the rows below j + 1 (s_i lives in place of
+//   r_i, which Gauss-Seidel boxes do not read again);
+// * row i itself belongs to two threads per box on two warps (two FP64 pipes): warp 0
+//   takes the lower ends (rd), warp 1 the upper ends (ru) -- the last prefix term, the
+//   j > i part of the fold, one quotient each, and their ends of the pieces x_i - q;
+//   warp 0 then intersects with X_i (integer compares) and records the result.
+// Every end is the same operation on the same operands as in the serial order, so the
+// results are bit-identical to it.  With gr.on (the owner's box asks for the two-box
 // split) a row whose Y_i meets X_i in two pieces records its gap RN(lower end of the
 // upper piece - upper end of the lower piece) in gr when it is wider than the widest so
 // far; the row itself still takes the hull.
 template <int N>
 __device__ __forceinline__ void gs_block(double *sd, int *si, int t, GapRec &gr) {
     using C = Cfg<N>;
-    constexpr int BB = C::BB, NT = C::NT;
+    constexpr int BB = C::BB, NT = C::NT, NP = N * (N - 1) / 2;
+    static_assert(NT >= 128, "the rows need warps 0 and 1 and at least one more");
     double *J = sd + C::JM;
+    double *F = sd + C::FR;    // r_i, then the running fold s_i
+    double *SX = sd + C::GB;   // lower ends of the row's pieces (B is not read any more)
     const int *run = si + C::I_RUN;
     const int *bad = si + C::I_BAD;
     int *empty = si + C::I_EMPTY;
@@ -407,85 +423,126 @@ __device__ __forceinline__ void gs_block(double *sd, int *si, int t, GapRec &gr)
         const int i = e / BB, b = e % BB;
         sd[C::YLO + i * BB + b] = sd[C::XLO + i * BB + b];
         sd[C::YHI + i * BB + b] = sd[C::XHI + i * BB + b];
+    }
+    for (int e = t; e < NP * BB; e += NT) {
+        const int pr = e / BB, b = e % BB;
         if (run[b] != 1 || bad[b]) continue;
-#pragma unroll
-        for (int j = 0; j < N; j++) {
-            if (j <= i) continue;
-            const double xc = sd[C::XC + j * BB + b];
-            const ivd d = iv_sub(ivd{sd[C::XLO + j * BB + b], sd[C::XHI + j * BB + b]}, ivd{xc, xc});
-            const ivd p = iv_mul(ivd{J[(2 * (i * N + j)) * BB + b], J[(2 * (i * N + j) + 1) * BB + b]}, d);
-            J[(2 * (i * N + j)) * BB + b] = p.lo;
-            J[(2 * (i * N + j) + 1) * BB + b] = p.hi;
+        int i = 0, r = pr;   // pair pr -> (i, j), j > i, row by row
+        while (r >= N - 1 - i) {
+            r -= N - 1 - i;
+            i++;
         }
+        const int j = i + 1 + r;
+        const double xc = sd[C::XC + j * BB + b];
+        const ivd d = iv_sub(ivd{sd[C::XLO + j * BB + b], sd[C::XHI + j * BB + b]}, ivd{xc, xc});
+        const ivd p = iv_mul(ivd{J[(2 * (i * N + j)) * BB + b], J[(2 * (i * N + j) + 1) * BB + b]}, d);
+        J[(2 * (i * N + j)) * BB + b] = p.lo;
+        J[(2 * (i * N + j) + 1) * BB + b] = p.hi;
     }
     __syncthreads();
     for (int i = 0; i < N; i++) {
-        if (t < BB) {
-            const int b = t;
-            if (run[b] == 1 && !bad[b] && !empty[b]) {
-                ivd s = {sd[C::FR + (2 * i) * BB + b], sd[C::FR + (2 * i + 1) * BB + b]};
+        if (t < 64) {
+            const int b = t & 31, up = t >> 5;   // up = 0: lower ends, 1: upper ends
+            const bool on = b < BB && run[b] == 1 && !bad[b] && !empty[b];
+            if (on) {
+                double v = F[(2 * i + up) * BB + b];
+                if (i > 0) {   // term j = i - 1 with the final Y_{i-1}
+                    const double xc = sd[C::XC + (i - 1) * BB + b];
+                    const ivd d = iv_sub(ivd{sd[C::YLO + (i - 1) * BB + b], sd[C::YHI + (i - 1) * BB + b]},
+                                         ivd{xc, xc});
+                    const ivd m = {J[(2 * (i * N + i - 1)) * BB + b], J[(2 * (i * N + i - 1) + 1) * BB + b]};
+                    v = up ? __dadd_ru(v, iv_mul_hi(m, d)) : __dadd_rd(v, iv_mul_lo(m, d));
+                }
 #pragma unroll
                 for (int j = 0; j < N; j++) {
-                    if (j == i) continue;
-                    s = iv_add(s, ivd{J[(2 * (i * N + j)) * BB + b], J[(2 * (i * N + j) + 1) * BB + b]});
+                    if (j <= i) continue;
+                    v = up ? __dadd_ru(v, J[(2 * (i * N + j) + 1) * BB + b]) : __dadd_rd(v, J[(2 * (i * N + j)) * BB + b]);
                 }
-                const ivd D = {J[(2 * (i * N + i)) * BB + b], J[(2 * (i * N + i) + 1) * BB + b]};
-                if (!(d_isnan(s.lo) || d_isnan(s.hi) || d_isnan(D.lo) || d_isnan(D.hi))) {
-                    ivd pc[2];
-                    const int np = iv_extdiv(s, D, pc);
-                    const double xc = sd[C::XC + i * BB + b];
-                    const double xlo = sd[C::XLO + i * BB + b], xhi = sd[C::XHI + i * BB + b];
-                    double lo = 0.0, hi = 0.0;
-                    bool any = false;
-                    double pa[2] = {0.0, 0.0}, pb[2] = {0.0, 0.0};   // the non-empty pieces
-                    int npc = 0;
+                F[(2 * i + up) * BB + b] = v;
+            }
+            pair_sync();
+            ivd s = {0.0, 0.0}, D = {0.0, 0.0};
+            bool ok = false;
+            int kind = XD_NONE, np = 0;
+            double xc = 0.0, yhi[2] = {0.0, 0.0};
+            if (on) {
+                s = ivd{F[(2 * i) * BB + b], F[(2 * i + 1) * BB + b]};
+                D = ivd{J[(2 * (i * N + i)) * BB + b], J[(2 * (i * N + i) + 1) * BB + b]};
+                ok = !(d_isnan(s.lo) || d_isnan(s.hi) || d_isnan(D.lo) || d_isnan(D.hi));
+            }
+            if (ok) {
+                const ExtDiv xd = extdiv_setup(s, D);
+                kind = xd.kind;
+                xc = sd[C::XC + i * BB + b];
+                ivd pc[2];
+                if (up) {   // upper quotient; lower ends of the pieces x_i - pc
+                    np = extdiv_pieces(kind, 0.0, __ddiv_ru(xd.un, xd.ud), pc);
 #pragma unroll
-                    for (int q = 0; q < 2; q++) {
-                        if (q >= np) continue;
-                        const ivd Y = iv_sub(ivd{xc, xc}, pc[q]);
-                        const double a0 = d_max(xlo, Y.lo), b0 = d_min(xhi, Y.hi);
-                        if (d_le(a0, b0)) {
-                            lo = any ? d_min(lo, a0) : a0;
-                            hi = any ? d_max(hi, b0) : b0;
-                            any = true;
-                            if (npc == 0) { pa[0] = a0; pb[0] = b0; }
-                            else { pa[1] = a0; pb[1] = b0; }
-                            npc++;
-                        }
-                    }
-                    if (!any) {
-                        empty[b] = 1;
-                    } else {
-                        if (gr.on && npc == 2) {
-                            const bool zero_up = !d_le(pa[0], pa[1]);   // piece 1 starts below piece 0
-                            const double llo = zero_up ? pa[1] : pa[0], lhi = zero_up ? pb[1] : pb[0];
-                            const double ulo = zero_up ? pa[0] : pa[1], uhi = zero_up ? pb[0] : pb[1];
-                            const double g = __dsub_rn(ulo, lhi);
-                            if (g > gr.w) {
-                                gr.w = g;
-                                gr.row = i;
-                                gr.llo = llo; gr.lhi = lhi; gr.ulo = ulo; gr.uhi = uhi;
-                            }
-                        }
-                        sd[C::YLO + i * BB + b] = lo;
-                        sd[C::YHI + i * BB + b] = hi;
+                    for (int q = 0; q < 2; q++)
+                        if (q < np) SX[q * BB + b] = __dsub_rd(xc, pc[q].hi);
+                } else {    // lower quotient; upper ends
+                    np = extdiv_pieces(kind, __ddiv_rd(xd.ln, xd.ld), 0.0, pc);
+#pragma unroll
+                    for (int q = 0; q < 2; q++)
+                        if (q < np) yhi[q] = __dsub_ru(xc, pc[q].lo);
+                }
+            }
+            pair_sync();
+            if (ok && !up) {
+                const double xlo = sd[C::XLO + i * BB + b], xhi = sd[C::XHI + i * BB + b];
+                double lo = 0.0, hi = 0.0;
+                bool any = false;
+                double pa[2] = {0.0, 0.0}, pb[2] = {0.0, 0.0};   // the non-empty pieces
+                int npc = 0;
+#pragma unroll
+                for (int q = 0; q < 2; q++) {
+                    if (q >= np) continue;
+                    const double a0 = d_max(xlo, SX[q * BB + b]), b0 = d_min(xhi, yhi[q]);
+                    if (d_le(a0, b0)) {
+                        lo = any ? d_min(lo, a0) : a0;
+                        hi = any ? d_max(hi, b0) : b0;
+                        any = true;
+                        if (npc == 0) { pa[0] = a0; pb[0] = b0; }
+                        else { pa[1] = a0; pb[1] = b0; }
+                        npc++;
                     }
                 }
+                if (!any) {
+                    empty[b] = 1;
+                } else {
+                    if (gr.on && npc == 2) {
+                        const bool zero_up = !d_le(pa[0], pa[1]);   // piece 1 starts below piece 0
+                        const double llo = zero_up ? pa[1] : pa[0], lhi = zero_up ? pb[1] : pb[0];
+                        const double ulo = zero_up ? pa[0] : pa[1], uhi = zero_up ? pb[0] : pb[1];
+                        const double g = __dsub_rn(ulo, lhi);
+                        if (g > gr.w) {
+                            gr.w = g;
+                            gr.row = i;
+                            gr.llo = llo; gr.lhi = lhi; gr.ulo = ulo; gr.uhi = uhi;
+                        }
+                    }
+                    sd[C::YLO + i * BB + b] = lo;
+                    sd[C::YHI + i * BB + b] = hi;
+                }
+            }
+        } else if (i > 0) {
+            // term j = i - 1 of the rows below i (row i's own is with its owners), on
+            // the warps of the other two sub-partitions first (warp w runs on
+            // sub-partition w % 4; warps 0 and 1 hold the row)
+            const int w = t >> 5, q = w & 3;
+            const int rank = q >= 2 ? 2 * (w >> 2) + q - 2 : C::NW / 2 + 2 * ((w >> 2) - 1) + q;
+            for (int e = rank * 32 + (t & 31); e < (N - 1 - i) * BB; e += NT - 64) {
+                const int i2 = i + 1 + e / BB, b = e % BB;
+                if (run[b] != 1 || bad[b] || empty[b]) continue;
+                const double xc = sd[C::XC + (i - 1) * BB + b];
+                const ivd d = iv_sub(ivd{sd[C::YLO + (i - 1) * BB + b], sd[C::YHI + (i - 1) * BB + b]}, ivd{xc, xc});
+                const ivd p = iv_mul(ivd{J[(2 * (i2 * N + i - 1)) * BB + b], J[(2 * (i2 * N + i - 1) + 1) * BB + b]}, d);
+                const ivd s = iv_add(ivd{F[(2 * i2) * BB + b], F[(2 * i2 + 1) * BB + b]}, p);
+                F[(2 * i2) * BB + b] = s.lo;
+                F[(2 * i2 + 1) * BB + b] = s.hi;
             }
         }
         __syncthreads();
-        if (i + 1 < N) {
-            for (int e = t; e < N * BB; e += NT) {
-                const int i2 = e / BB, b = e % BB;
-                if (i2 <= i || run[b] != 1 || bad[b] || empty[b]) continue;
-                const double xc = sd[C::XC + i * BB + b];
-                const ivd d = iv_sub(ivd{sd[C::YLO + i * BB + b], sd[C::YHI + i * BB + b]}, ivd{xc, xc});
-                const ivd p = iv_mul(ivd{J[(2 * (i2 * N + i)) * BB + b], J[(2 * (i2 * N + i) + 1) * BB + b]}, d);
-                J[(2 * (i2 * N + i)) * BB + b] = p.lo;
-                J[(2 * (i2 * N + i) + 1) * BB + b] = p.hi;
-            }
-            __syncthreads();
-        }
     }
 }
 

@@ -52,24 +52,52 @@ __device__ __forceinline__ ivd iv_sub(ivd x, ivd y) { return {__dsub_rd(x.lo, y.
 // would re-issue its FP64 instructions at full warp cost.  The second pair only differs
 // from the first when both operands straddle 0.  Classes: P = lo >= 0, else N = hi <= 0,
 // else S (lo < 0 < hi); P is tested first, as in the serial definition.
-__device__ __forceinline__ ivd iv_mul(ivd x, ivd y) {
+// Endpoint operands of the product x y: the lower end is min(rd(la lb), rd(la2 lb2)),
+// the upper end max(ru(ua ub), ru(ua2 ub2)); the second pair differs from the first only
+// when both operands straddle 0 (`both`).
+struct MulSel {
+    double la, lb, la2, lb2, ua, ub, ua2, ub2;
+    bool both;
+};
+__device__ __forceinline__ MulSel mul_sel(ivd x, ivd y) {
     const bool xp = !d_neg(x.lo), xn = !xp && !d_pos(x.hi), xs = !xp && !xn;
     const bool yp = !d_neg(y.lo), yn = !yp && !d_pos(y.hi), ys = !yp && !yn;
+    MulSel m;
+    m.both = xs && ys;
     // lower end: xP: (yP ? lo : hi) * y.lo;  xN: (yN ? hi : lo) * y.hi;
     //            xS: yN ? hi * lo : lo * hi (and hi * lo as well when y straddles)
-    const double la = xp ? (yp ? x.lo : x.hi) : (yn ? x.hi : x.lo);
-    const double lb = xp ? y.lo : (xn ? y.hi : (yn ? y.lo : y.hi));
-    const double la2 = (xs && ys) ? x.hi : la, lb2 = (xs && ys) ? y.lo : lb;
+    m.la = xp ? (yp ? x.lo : x.hi) : (yn ? x.hi : x.lo);
+    m.lb = xp ? y.lo : (xn ? y.hi : (yn ? y.lo : y.hi));
+    m.la2 = m.both ? x.hi : m.la;
+    m.lb2 = m.both ? y.lo : m.lb;
     // upper end: xP: (yN ? lo : hi) * y.hi;  xN: (yP ? hi : lo) * y.lo;
     //            xS: yP ? hi * hi : lo * lo (and hi * hi as well when y straddles)
-    const double ua = xp ? (yn ? x.lo : x.hi) : (xn ? (yp ? x.hi : x.lo) : (yp ? x.hi : x.lo));
-    const double ub = xp ? y.hi : (xn ? y.lo : (yp ? y.hi : y.lo));
-    const double ua2 = (xs && ys) ? x.hi : ua, ub2 = (xs && ys) ? y.hi : ub;
-    const double l1 = __dmul_rd(la, lb), u1 = __dmul_ru(ua, ub);
+    m.ua = xp ? (yn ? x.lo : x.hi) : (xn ? (yp ? x.hi : x.lo) : (yp ? x.hi : x.lo));
+    m.ub = xp ? y.hi : (xn ? y.lo : (yp ? y.hi : y.lo));
+    m.ua2 = m.both ? x.hi : m.ua;
+    m.ub2 = m.both ? y.hi : m.ub;
+    return m;
+}
+__device__ __forceinline__ ivd iv_mul(ivd x, ivd y) {
+    const MulSel m = mul_sel(x, y);
+    const double l1 = __dmul_rd(m.la, m.lb), u1 = __dmul_ru(m.ua, m.ub);
     // the second pair only when some lane of the warp has both operands straddling 0
     // (for the other lanes it repeats the first pair, so their result is unchanged)
-    if (__any_sync(__activemask(), xs && ys)) return {d_min(l1, __dmul_rd(la2, lb2)), d_max(u1, __dmul_ru(ua2, ub2))};
+    if (__any_sync(__activemask(), m.both)) return {d_min(l1, __dmul_rd(m.la2, m.lb2)), d_max(u1, __dmul_ru(m.ua2, m.ub2))};
     return {l1, u1};
+}
+// the lower / upper end of iv_mul(x, y) alone (the same value, half the multiplies)
+__device__ __forceinline__ double iv_mul_lo(ivd x, ivd y) {
+    const MulSel m = mul_sel(x, y);
+    const double l1 = __dmul_rd(m.la, m.lb);
+    if (__any_sync(__activemask(), m.both)) return d_min(l1, __dmul_rd(m.la2, m.lb2));
+    return l1;
+}
+__device__ __forceinline__ double iv_mul_hi(ivd x, ivd y) {
+    const MulSel m = mul_sel(x, y);
+    const double u1 = __dmul_ru(m.ua, m.ub);
+    if (__any_sync(__activemask(), m.both)) return d_max(u1, __dmul_ru(m.ua2, m.ub2));
+    return u1;
 }
 
 // point b times interval y (b a double): two products
@@ -142,37 +170,50 @@ __device__ __forceinline__ ivd iv_div(ivd x, ivd y) {
 // x > 0: y = [c,0] -> (-inf, lo/c], c < 0 < d -> (-inf, lo/c] u [lo/d, +inf),
 // y = [0,d] -> [lo/d, +inf).  Finite ends round outward.  Every case needs at most one
 // round-down and one round-up quotient; both are issued once with selected operands.
-__device__ __forceinline__ int iv_extdiv(ivd x, ivd y, ivd *p) {
-    const double inf = __longlong_as_double(0x7FF0000000000000LL);
+// The case and the quotient operands: qd = rd(ln / ld), qu = ru(un / ud).
+enum : int { XD_ORD, XD_WHOLE, XD_NONE, XD_UP, XD_DOWN, XD_TWO };   // [qd,qu] R {} [qd,inf) (-inf,qu] both
+struct ExtDiv {
+    double ln, ld, un, ud;
+    int kind;
+};
+__device__ __forceinline__ ExtDiv extdiv_setup(ivd x, ivd y) {
     const bool ordinary = d_pos(y.lo) || d_neg(y.hi);
     const bool whole = !ordinary && !d_pos(x.lo) && !d_neg(x.hi);
     const bool ylo0 = d_iszero(y.lo), yhi0 = d_iszero(y.hi);
     const bool xneg = d_neg(x.hi);                    // else x > 0 in the extended cases
-    double ln, ld, un, ud;
-    div_operands(x, y, ln, ld, un, ud);
+    ExtDiv e;
+    div_operands(x, y, e.ln, e.ld, e.un, e.ud);
     if (!ordinary) {
         // rd quotient: x < 0: hi / c;  x > 0: lo / d.   ru quotient: x < 0: hi / d;  x > 0: lo / c
-        ln = xneg ? x.hi : x.lo;
-        ld = xneg ? y.lo : y.hi;
-        un = xneg ? x.hi : x.lo;
-        ud = xneg ? y.hi : y.lo;
+        e.ln = xneg ? x.hi : x.lo;
+        e.ld = xneg ? y.lo : y.hi;
+        e.un = xneg ? x.hi : x.lo;
+        e.ud = xneg ? y.hi : y.lo;
     }
-    const double qd = __ddiv_rd(ln, ld), qu = __ddiv_ru(un, ud);
-    if (ordinary) { p[0] = {qd, qu}; return 1; }
-    if (whole) { p[0] = {-inf, inf}; return 1; }
-    if (ylo0 && yhi0) return 0;
-    if (xneg) {
-        if (yhi0) { p[0] = {qd, inf}; return 1; }
-        if (ylo0) { p[0] = {-inf, qu}; return 1; }
-        p[0] = {-inf, qu};
-        p[1] = {qd, inf};
-        return 2;
+    e.kind = ordinary ? XD_ORD : whole ? XD_WHOLE : (ylo0 && yhi0) ? XD_NONE
+           : yhi0 ? (xneg ? XD_UP : XD_DOWN) : ylo0 ? (xneg ? XD_DOWN : XD_UP) : XD_TWO;
+    // a quotient the case does not use gets 1 / 1 (its operands may hold a zero divisor,
+    // which would take the division's special-case path for nothing)
+    if (e.kind == XD_WHOLE || e.kind == XD_NONE || e.kind == XD_DOWN) e.ln = e.ld = 1.0;
+    if (e.kind == XD_WHOLE || e.kind == XD_NONE || e.kind == XD_UP) e.un = e.ud = 1.0;
+    return e;
+}
+// the pieces from the two quotients; returns their count
+__device__ __forceinline__ int extdiv_pieces(int kind, double qd, double qu, ivd *p) {
+    const double inf = __longlong_as_double(0x7FF0000000000000LL);
+    switch (kind) {
+        case XD_ORD: p[0] = {qd, qu}; return 1;
+        case XD_WHOLE: p[0] = {-inf, inf}; return 1;
+        case XD_NONE: return 0;
+        case XD_UP: p[0] = {qd, inf}; return 1;
+        case XD_DOWN: p[0] = {-inf, qu}; return 1;
+        default: p[0] = {-inf, qu}; p[1] = {qd, inf}; return 2;
     }
-    if (yhi0) { p[0] = {-inf, qu}; return 1; }
-    if (ylo0) { p[0] = {qd, inf}; return 1; }
-    p[0] = {-inf, qu};
-    p[1] = {qd, inf};
-    return 2;
+}
+__device__ __forceinline__ int iv_extdiv(ivd x, ivd y, ivd *p) {
+    const ExtDiv e = extdiv_setup(x, y);
+    const double qd = __ddiv_rd(e.ln, e.ld), qu = __ddiv_ru(e.un, e.ud);
+    return extdiv_pieces(e.kind, qd, qu, p);
 }
 
 // ---- FP32 interval operations (prefilter) -----------------------------------------

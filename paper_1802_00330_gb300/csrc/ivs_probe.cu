@@ -42,6 +42,24 @@ __global__ void k_probe_fp32(float seed, float *sink) {
     if (s == 12345.678f) sink[0] = s;
 }
 
+// directed (kind 4: alternating __ddiv_rd / __ddiv_ru) or round-to-nearest (kind 5)
+// FP64 division, the same 8 independent chains per thread; values stay near 1
+__global__ void k_probe_div(double seed, double *sink, int directed) {
+    double x[kProbeChains];
+#pragma unroll
+    for (int c = 0; c < kProbeChains; c++) x[c] = seed + c * 1e-3 + threadIdx.x * 1e-9;
+    const double a = 1.0000000001, b = 0.9999999999;
+    for (int i = 0; i < kProbeIters / 8; i++) {
+#pragma unroll
+        for (int c = 0; c < kProbeChains; c++)
+            x[c] = directed ? __ddiv_ru(__ddiv_rd(x[c], a), b) : __ddiv_rn(__ddiv_rn(x[c], a), b);
+    }
+    double s = 0;
+#pragma unroll
+    for (int c = 0; c < kProbeChains; c++) s += x[c];
+    if (s == 12345.678) sink[0] = s;
+}
+
 cudaError_t run_probe(int kind, int num_sms, double *ops, float *ms) {
     void *sink = nullptr;
     cudaError_t e = cudaMalloc(&sink, 64);
@@ -53,6 +71,7 @@ cudaError_t run_probe(int kind, int num_sms, double *ops, float *ms) {
     for (int rep = 0; rep < 3; rep++) {   // first launches warm up clocks and caches
         cudaEventRecord(a);
         if (kind == 0) k_probe_fp64<<<blocks, threads>>>(1.0, (double *)sink, 32);
+        else if (kind == 4 || kind == 5) k_probe_div<<<blocks, threads>>>(1.0, (double *)sink, kind == 4);
         else if (kind >= 2) k_probe_fp64<<<blocks, threads>>>(1.0, (double *)sink, kind == 2 ? 8 : 1);
         else k_probe_fp32<<<blocks, threads>>>(1.0f, (float *)sink);
         cudaEventRecord(b);
@@ -61,7 +80,7 @@ cudaError_t run_probe(int kind, int num_sms, double *ops, float *ms) {
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
     const int lanes = kind == 2 ? 8 : kind == 3 ? 1 : 32;
-    *ops = (double)blocks * (threads / 32) * lanes * kProbeIters * kProbeChains * 2.0;
+    *ops = (double)blocks * (threads / 32) * lanes * (kind >= 4 ? kProbeIters / 8 : kProbeIters) * kProbeChains * 2.0;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaFree(sink);

@@ -194,6 +194,7 @@ int ivs_server::init() {
     a.rg.cursor = (unsigned long long *)(rg_mem + 3 * S);
     a.rg.prefix = rg_mem + 4 * S;
     a.rg.n = S;
+    a.rg.fair_share = cfg.schedule == 1 ? 1 : 0;
     free_regions[0] = q_cap;
     region_of.assign((size_t)S, {0, 0});
     CUDA_TRY(cudaMallocHost((void **)&h_region, 2 * (size_t)S * sizeof(int64_t)));
@@ -514,9 +515,10 @@ int ivs_server_create(const ivs_server_cfg *cfg, ivs_server **out) {
         if (cfg->sweeps_per_step > 0) c.sweeps_per_step = cfg->sweeps_per_step;
         if (cfg->reserve_factor > 0) c.reserve_factor = cfg->reserve_factor;
         if (cfg->min_region_entries > 0) c.min_region_entries = cfg->min_region_entries;
+        c.schedule = cfg->schedule;
         c.device = cfg->device;
     }
-    if (c.max_vars > kMaxVars || c.max_slots > 65536 || c.wave_children < ((int64_t)1 << c.max_vars))
+    if (c.max_vars > kMaxVars || c.max_slots > 65536 || c.schedule < 0 || c.schedule > 1 || c.wave_children < ((int64_t)1 << c.max_vars))
         return fail(IVS_ERR_INVALID, "bad server configuration");
     std::unique_ptr<ivs_server> sv(new (std::nothrow) ivs_server());
     if (!sv) return fail(IVS_ERR_NOMEM, "host allocation");

@@ -49,11 +49,14 @@ def mix_systems():
     return small
 
 
-def test_alone_equals_in_the_mix(B):
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_alone_equals_in_the_mix(B, schedule):
+    """Both schedules (least attained service first; rotating equal shares) leave every
+    result as it is alone."""
     systems = mix_systems()
     targets = [0, 7, 19, 33]
     alone = {i: B.solve(systems[i]) for i in targets}
-    sv = B.Server(workspace_bytes=1 << 30, max_slots=64, wave_children=1 << 20, max_vars=8)
+    sv = B.Server(workspace_bytes=1 << 30, max_slots=64, wave_children=1 << 20, max_vars=8, schedule=schedule)
     try:
         tickets = [sv.submit(s) for s in systems]
         results = wait_all(sv, tickets)
@@ -147,13 +150,15 @@ def test_time_budget_frees_the_queue(B):
         sv.close()
 
 
-def test_each_request_gets_its_share(B):
-    """Every request in flight has its own queue region and a fair share of each sweep:
-    small requests interleaved with hard ones in one burst finish promptly and exactly
-    while the hard ones run until their time budget."""
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_each_request_gets_its_share(B, schedule):
+    """Every request in flight has its own queue region and a share of each sweep (the
+    least served first, or equal shares): small requests interleaved with hard ones in
+    one burst finish promptly and exactly while the hard ones run until their time
+    budget."""
     hard = [synth.config_n10()] * 3
     small = synth.config_batched(count=12, seed=1212, n_range=(2, 4))
-    sv = B.Server(workspace_bytes=1 << 31, max_slots=32, wave_children=1 << 20, max_vars=10)
+    sv = B.Server(workspace_bytes=1 << 31, max_slots=32, wave_children=1 << 20, max_vars=10, schedule=schedule)
     try:
         tickets, kinds = [], []
         for k, s in enumerate(small):
