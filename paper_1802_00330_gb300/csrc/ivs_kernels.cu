@@ -449,6 +449,20 @@ __device__ __forceinline__ void push_surv(const SweepArgs &a, WaveCtl *ctl, int 
     }
 }
 
+// undecided children for k_eval64 (warp-aggregated append)
+__device__ __forceinline__ void push_cand(const SweepArgs &a, WaveCtl *ctl, bool cand, Surv sv) {
+    const unsigned cm = __ballot_sync(kFull, cand);
+    if (!cm) return;
+    unsigned long long pos = 0;
+    if (lane_id() == 0) pos = atomicAdd((unsigned long long *)&ctl->cand_count, (unsigned long long)__popc(cm));
+    pos = __shfl_sync(kFull, pos, 0);
+    if (cand) {
+        const unsigned long long k = pos + __popc(cm & lanemask_lt());
+        if ((long long)k < a.surv_cap) a.cand[k] = sv;
+        else ctl->error = 1;
+    }
+}
+
 // The children of one parent, evaluated by a group of threads: one warp (GROUP = 32) or
 // the whole block.  r = the thread's rank in the group, G = the group size; every
 // thread of the group runs this with the same pi.  Three forms: the FP32 shadow (decides
@@ -529,12 +543,31 @@ __device__ __forceinline__ void eval_parent(const SweepArgs &a, WaveCtl *ctl, co
         }
         group_sync<BLOCK>();
     }
-    for (unsigned c0 = 0; c0 < fan; c0 += G) {
+    // two children per thread (c0 + r and c0 + G + r) on the table path with a child-index
+    // table when the fan-out fills two rounds of the group: two independent chains
+    const bool pair = use_tv && S.n_cix > 0 && fan >= 2 * G;
+    for (unsigned c0 = 0; c0 < fan; c0 += pair ? 2 * G : G) {
         const bool active = c0 + r < fan;
         const unsigned c = child_bits(S, meta, c0 + r);
         bool keep = false, cand = false;
+        const bool active2 = pair && c0 + G + r < fan;
+        const unsigned c2 = pair ? child_bits(S, meta, c0 + G + r) : 0u;
+        bool keep2 = false, cand2 = false;
         if (active) {
-            if (use_tv) {
+            if (pair) {
+                int d2 = 0;
+                const int d = decide_from_table2(T, S, s_tv, c, c2, active2, d2);
+                keep = d == 1;
+                cand = d == 2;
+                cnt_pre += d == 0 ? 1u : 0u;
+                cnt_sh += keep ? 1u : 0u;
+                if (active2) {
+                    keep2 = d2 == 1;
+                    cand2 = d2 == 2;
+                    cnt_pre += d2 == 0 ? 1u : 0u;
+                    cnt_sh += keep2 ? 1u : 0u;
+                }
+            } else if (use_tv) {
                 const int d = decide_from_table(T, S, s_tv, c);
                 keep = d == 1;
                 cand = d == 2;
@@ -556,16 +589,10 @@ __device__ __forceinline__ void eval_parent(const SweepArgs &a, WaveCtl *ctl, co
             }
         }
         push_surv(a, ctl, n, keep, Surv{(uint32_t)pi, c});
-        const unsigned cm = __ballot_sync(kFull, cand);
-        if (cm) {
-            unsigned long long pos = 0;
-            if (lane == 0) pos = atomicAdd((unsigned long long *)&ctl->cand_count, (unsigned long long)__popc(cm));
-            pos = __shfl_sync(kFull, pos, 0);
-            if (cand) {
-                const unsigned long long k = pos + __popc(cm & lanemask_lt());
-                if ((long long)k < a.surv_cap) a.cand[k] = Surv{(uint32_t)pi, c};
-                else ctl->error = 1;
-            }
+        push_cand(a, ctl, cand, Surv{(uint32_t)pi, c});
+        if (pair) {
+            push_surv(a, ctl, n, keep2, Surv{(uint32_t)pi, c2});
+            push_cand(a, ctl, cand2, Surv{(uint32_t)pi, c2});
         }
     }
     cnt_pre = __reduce_add_sync(kFull, cnt_pre);
