@@ -463,6 +463,33 @@ __device__ __forceinline__ void push_cand(const SweepArgs &a, WaveCtl *ctl, bool
     }
 }
 
+// Children c0 + k G + r (k < K) of parent pi per thread, decided K at a time from the
+// parent's table (decide_from_table_k), then appended to the survivor / candidate lists.
+template <int K>
+__device__ __forceinline__ void table_children(const SweepArgs &a, WaveCtl *ctl, const SysTab &T, const DevSys &S,
+                                               const float4 *tv, uint32_t meta, int64_t pi, int n, unsigned fan,
+                                               unsigned r, unsigned G, unsigned &cnt_pre, unsigned &cnt_sh) {
+    for (unsigned c0 = 0; c0 < fan; c0 += K * G) {
+        unsigned c[K];
+        bool want[K];
+        int d[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            c[k] = child_bits(S, meta, c0 + k * G + r);
+            want[k] = c0 + k * G + r < fan;
+        }
+        decide_from_table_k<K>(T, S, tv, c, want, d);
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const bool keep = want[k] && d[k] == 1, cand = want[k] && d[k] == 2;
+            cnt_pre += (want[k] && d[k] == 0) ? 1u : 0u;
+            cnt_sh += keep ? 1u : 0u;
+            push_surv(a, ctl, n, keep, Surv{(uint32_t)pi, c[k]});
+            push_cand(a, ctl, cand, Surv{(uint32_t)pi, c[k]});
+        }
+    }
+}
+
 // The children of one parent, evaluated by a group of threads: one warp (GROUP = 32) or
 // the whole block.  r = the thread's rank in the group, G = the group size; every
 // thread of the group runs this with the same pi.  Three forms: the FP32 shadow (decides
@@ -543,31 +570,20 @@ __device__ __forceinline__ void eval_parent(const SweepArgs &a, WaveCtl *ctl, co
         }
         group_sync<BLOCK>();
     }
-    // two children per thread (c0 + r and c0 + G + r) on the table path with a child-index
-    // table when the fan-out fills two rounds of the group: two independent chains
-    const bool pair = use_tv && S.n_cix > 0 && fan >= 2 * G;
-    for (unsigned c0 = 0; c0 < fan; c0 += pair ? 2 * G : G) {
+    // K children per thread (c0 + k G + r, k < K) on the table path with a child-index
+    // table when the fan-out fills K rounds of the group: K independent chains
+    const bool cix_tab = use_tv && S.n_cix > 0;
+    if (cix_tab && fan >= 4 * G) {
+        table_children<4>(a, ctl, T, S, s_tv, meta, pi, n, fan, r, G, cnt_pre, cnt_sh);
+    } else if (cix_tab && fan >= 2 * G) {
+        table_children<2>(a, ctl, T, S, s_tv, meta, pi, n, fan, r, G, cnt_pre, cnt_sh);
+    } else {
+    for (unsigned c0 = 0; c0 < fan; c0 += G) {
         const bool active = c0 + r < fan;
         const unsigned c = child_bits(S, meta, c0 + r);
         bool keep = false, cand = false;
-        const bool active2 = pair && c0 + G + r < fan;
-        const unsigned c2 = pair ? child_bits(S, meta, c0 + G + r) : 0u;
-        bool keep2 = false, cand2 = false;
         if (active) {
-            if (pair) {
-                int d2 = 0;
-                const int d = decide_from_table2(T, S, s_tv, c, c2, active2, d2);
-                keep = d == 1;
-                cand = d == 2;
-                cnt_pre += d == 0 ? 1u : 0u;
-                cnt_sh += keep ? 1u : 0u;
-                if (active2) {
-                    keep2 = d2 == 1;
-                    cand2 = d2 == 2;
-                    cnt_pre += d2 == 0 ? 1u : 0u;
-                    cnt_sh += keep2 ? 1u : 0u;
-                }
-            } else if (use_tv) {
+            if (use_tv) {
                 const int d = decide_from_table(T, S, s_tv, c);
                 keep = d == 1;
                 cand = d == 2;
@@ -590,10 +606,7 @@ __device__ __forceinline__ void eval_parent(const SweepArgs &a, WaveCtl *ctl, co
         }
         push_surv(a, ctl, n, keep, Surv{(uint32_t)pi, c});
         push_cand(a, ctl, cand, Surv{(uint32_t)pi, c});
-        if (pair) {
-            push_surv(a, ctl, n, keep2, Surv{(uint32_t)pi, c2});
-            push_cand(a, ctl, cand2, Surv{(uint32_t)pi, c2});
-        }
+    }
     }
     cnt_pre = __reduce_add_sync(kFull, cnt_pre);
     cnt_ev = __reduce_add_sync(kFull, cnt_ev);

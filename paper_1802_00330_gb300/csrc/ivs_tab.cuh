@@ -257,36 +257,50 @@ __device__ __forceinline__ int decide_from_table(const SysTab &T, const DevSys &
     return undecided ? 2 : 1;
 }
 
-// The same decision for two children c0, c1 of one parent at once (child-index table
-// present), each exactly as decide_from_table: the two sums of an equation are
-// independent chains of loads and adds, so one thread overlaps their latencies.  An
-// equation is evaluated while either child is undecided; a decided child's sums are
-// ignored.  Returns d0 and writes d1 (want1 = false: c1 is not a child, d1 = 0).
-__device__ __forceinline__ int decide_from_table2(const SysTab &T, const DevSys &S, const float4 *tv, unsigned c0,
-                                                  unsigned c1, bool want1, int &d1) {
-    int r0 = -1, r1 = want1 ? -1 : 0;   // -1: no equation excluded yet
-    bool u0 = false, u1 = false;
-    for (int i = 0; i < S.m && (r0 < 0 || r1 < 0); i++) {
+// The same decision for K children c[0..K) of one parent at once (child-index table
+// present), each exactly as decide_from_table: the K sums of an equation are independent
+// chains of loads and adds, so one thread overlaps their latencies.  An equation is
+// evaluated while any wanted child is undecided; a decided child's sums are ignored.
+// want[k] = false: c[k] is not a child (d[k] = 0).
+template <int K>
+__device__ __forceinline__ void decide_from_table_k(const SysTab &T, const DevSys &S, const float4 *tv,
+                                                    const unsigned (&c)[K], const bool (&want)[K], int (&d)[K]) {
+    int rs[K];      // -1: no equation excluded yet
+    bool und[K];
+    int open = 0;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        rs[k] = want[k] ? -1 : 0;
+        und[k] = false;
+        open += want[k] ? 1 : 0;
+    }
+    for (int i = 0; i < S.m && open > 0; i++) {
         const int t0 = T.poly_off[S.f_poly + i], t1 = T.poly_off[S.f_poly + i + 1];
-        shv a0 = {0.f, 0.f, 0.f, 0.f}, a1 = {0.f, 0.f, 0.f, 0.f};
+        shv acc[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) acc[k] = shv{0.f, 0.f, 0.f, 0.f};
         for (int t = t0; t < t1; t++) {
             const uint16_t *row = T.cix + ((unsigned)t << S.n);
-            const float4 v0 = tv[row[c0]], v1 = tv[row[c1]];
-            const shv s0 = {v0.x, v0.y, v0.z, v0.w}, s1 = {v1.x, v1.y, v1.z, v1.w};
-            a0 = (t == t0) ? s0 : sh_add(a0, s0);
-            a1 = (t == t0) ? s1 : sh_add(a1, s1);
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const float4 v = tv[row[c[k]]];
+                const shv s = {v.x, v.y, v.z, v.w};
+                acc[k] = (t == t0) ? s : sh_add(acc[k], s);
+            }
         }
-        if (r0 < 0) {
-            if (a0.ld > 0.0f || a0.hu < 0.0f) r0 = 0;
-            else if (!(a0.lu <= 0.0f && a0.hd >= 0.0f)) u0 = true;
-        }
-        if (r1 < 0) {
-            if (a1.ld > 0.0f || a1.hu < 0.0f) r1 = 0;
-            else if (!(a1.lu <= 0.0f && a1.hd >= 0.0f)) u1 = true;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            if (rs[k] >= 0) continue;
+            if (acc[k].ld > 0.0f || acc[k].hu < 0.0f) {
+                rs[k] = 0;
+                open--;
+            } else if (!(acc[k].lu <= 0.0f && acc[k].hd >= 0.0f)) {
+                und[k] = true;
+            }
         }
     }
-    d1 = r1 >= 0 ? r1 : (u1 ? 2 : 1);
-    return r0 >= 0 ? r0 : (u0 ? 2 : 1);
+#pragma unroll
+    for (int k = 0; k < K; k++) d[k] = rs[k] >= 0 ? rs[k] : (und[k] ? 2 : 1);
 }
 
 }  // namespace ivs
