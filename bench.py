@@ -124,9 +124,11 @@ def hs_ops(s, krawczyk=False):
 TRAFFIC = {
     ("n6", "hs_n6"): {"sources_sha256": "62891eeae8663b1de6d2d8d6266de4e64e29152cb3868fb6bbab36a76f7ec840",
                       "bytes_per_launch": 485350, "default_options_only": True},
-    # profiles/k_hs_n8_batched.md: 13.02 GB over 112,757,665 n = 8 boxes of all launches
-    ("batched", "hs_n8"): {"sources_sha256": "d2e66d7d4971a3118ca76bb77801e1102fc39b081d466a1d5fb5e977a9d66458",
-                           "bytes_per_hs_box": 115.45, "default_options_only": True},
+    # profiles/k_hs_n8_batched.md: 6.479 GB over 112,757,665 n = 8 boxes of all launches of a
+    # solve with sweeps of 2^24 children (valid for that sweep size only: smaller sweeps
+    # re-read more of their parents from DRAM)
+    ("batched", "hs_n8"): {"sources_sha256": "c44aac276b43290460c0650e3d9a0e8ae810783df0d16dae8a9dc0db22b76c93",
+                           "bytes_per_hs_box": 57.46, "default_options_only": True, "wave_children": 1 << 24},
 }
 KERNEL_SOURCES = ("ivs_hs.cuh", "ivs_tab.cuh", "ivs_interval.cuh", "ivs_internal.h", "ivs_kernels.cuh")
 
@@ -153,9 +155,11 @@ def hs_sources_sha(read=None, files=KERNEL_SOURCES):
     return h.hexdigest()
 
 
-def traffic_of(workload_name, kernel, default_options=True, hs_boxes_per_launch=None):
+def traffic_of(workload_name, kernel, default_options=True, hs_boxes_per_launch=None, wave_children=None):
     rec = TRAFFIC.get((workload_name, kernel))
     if rec is None or (rec.get("default_options_only") and not default_options):
+        return None
+    if "wave_children" in rec and rec["wave_children"] != wave_children:
         return None
     files = rec.get("files", KERNEL_SOURCES)
     if rec["sources_sha256"] != hs_sources_sha(files=files):
@@ -604,7 +608,7 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
     roofline = dict(dom)
     roofline.update({
         "traffic": traffic_of(args.workload, dom["kernel"], not (args.centred or args.krawczyk),
-                              dom.get("hs_boxes_per_launch")),
+                              dom.get("hs_boxes_per_launch"), args.wave_children),
         "op_convention": "one directed add or multiply = 1 flop (no FMA on the path)",
         "peak_source": f"measured in this run: directed {'__fadd_rd/__fmul_ru' if dom['pipe'] == 'fp32' else '__dadd_rd/__dmul_ru'} probe",
         "work": ("natural-form operations per child through the FP32 stage" if dom["kernel"] == "eval" else

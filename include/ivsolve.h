@@ -217,9 +217,11 @@ void ivs_plan_destroy(ivs_plan *p);
 /* Autotuner of the batching form (no paper counterpart): for the given systems it runs
  * short trial solves (each system capped at trial_boxes processed boxes) with every
  * combination of wave_children in {2^20, 2^22, 2^24} and evaluation grids of {4, 8, 16}
- * blocks per SM, and writes the configuration with the highest boxes/s to *best (its
- * other fields zero) and that rate to *best_rate.  The choices only schedule work:
- * results do not depend on them. */
+ * blocks per SM (each timed as the faster of two runs after a warm-up), and writes to *best
+ * (its other fields zero) the configuration with the largest wave_children among those
+ * within 3% of the highest boxes/s (the capped trial runs fewer sweeps than a full solve,
+ * so it undercounts the fixed cost per sweep), and its rate to *best_rate.  The choices
+ * only schedule work: results do not depend on them. */
 int ivs_autotune(int32_t n_sys, const ivs_system *systems, const double *const *box_lo,
                  const double *const *box_hi, const ivs_options *opts, int32_t opts_stride,
                  int64_t trial_boxes, ivs_plan_cfg *best, double *best_rate);
