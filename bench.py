@@ -6,8 +6,9 @@ and refill) for every system of it -- with the systems already resident on the d
 
 Default workload: the batching form, 4096 seeded systems (n ~ U{2..8}, 4-10 monomials per
 equation, degree <= 3, integer coefficients in [-5,5], one planted root each, box [-4,4]^n,
-tol 1e-6) solved in one device run under one captured graph, sweep size and evaluation grid
-picked by the autotuner.  Beside the timed FP32-prefilter form the line carries the plain
+tol 1e-6) solved in one device run under one captured graph, sweeps of 2^24 children and
+4 evaluation blocks per SM (the fastest measured on this batch; --autotune picks them with
+ivs_autotune instead).  Beside the timed FP32-prefilter form the line carries the plain
 FP64 path on the same systems, the plain FP64 per-system path (ivs_solve one system at a
 time) on a systematic sample of them, the end-to-end rate through the public host API, the
 roofline of every kernel class, the serial oracle on the host cores, and the single n=6
@@ -53,7 +54,7 @@ def workload(name, batched_count=4096):
     if name == "batched":
         return synth.config_batched(count=batched_count), (
             f"batched: {batched_count} seeded systems, n~U{{2..8}}, 4-10 monomials/eq, deg<=3, int coef [-5,5], "
-            "planted roots, box [-4,4]^n, tol 1e-6, HS on, FP32 prefilter, one device run, autotuned sweep size")
+            "planted roots, box [-4,4]^n, tol 1e-6, HS on, FP32 prefilter, one device run, sweeps of 2^24 children")
     if name == "paper":
         import dataclasses
         systems = [dataclasses.replace(synth.load_fixture(os.path.join(ROOT, "tests", "golden", f"{k}.txt")), tol=1e-3)
@@ -468,10 +469,18 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
 
     stream = torch.cuda.Stream()
     tuned = None
-    if multi and not args.wave_children:
-        # batching form: the autotuner picks the sweep size and evaluation grid (outside timing)
+    if multi and args.autotune and not args.wave_children:
+        # the autotuner picks the sweep size and evaluation grid (outside timing)
         tuned = B.autotune(systems[: min(len(systems), 256)], trial_boxes=100_000)
         args.wave_children = int(tuned["wave_children"])
+    elif multi and not args.wave_children:
+        # batching form, fixed: sweeps of 2^24 children and 4 evaluation blocks per SM, the
+        # fastest measured on the full 4096-system batch (42.5 s per step against 47.8 s
+        # with the 2^22 / 8-per-SM pick of a short capped trial, which cannot see what
+        # large sweeps save over a 10^10-box solve)
+        props = torch.cuda.get_device_properties(local_rank)
+        tuned = {"wave_children": 1 << 24, "eval_blocks": 4 * props.multi_processor_count, "source": "fixed"}
+        args.wave_children = tuned["wave_children"]
     base_opts = {}
     if args.centred:
         base_opts["centred_form"] = 1
@@ -651,7 +660,7 @@ def run_gpu(args, systems, desc, rank, world, local_rank):
             "config": config_of(args, systems, desc, world),
             "systems_per_s": sys_per_s,
             "boxes_per_step": boxes / args.steps,
-            "autotuned": tuned,
+            "sweep_config": tuned,
             "plain_fp64_path": {"value": b64 / t64_total, "unit": "boxes/s", "steps": len(t64),
                                 "systems_per_s": world * len(systems) * len(t64) / t64_total,
                                 "ms_per_step": 1e3 * t64_total / len(t64), "results": "identical"},
@@ -883,6 +892,8 @@ def main():
     ap.add_argument("--workload", default="batched")
     ap.add_argument("--impl", default="ivsolve")
     ap.add_argument("--wave-children", type=int, default=0)
+    ap.add_argument("--autotune", action="store_true",
+                    help="batched forms: pick sweep size and grid with ivs_autotune on 256 systems")
     ap.add_argument("--aux-steps", type=int, default=0,
                     help="steps of the auxiliary passes (plain FP64, e2e, per-kernel profile); "
                          "0 = 1 for multi-system workloads, --steps otherwise")
