@@ -123,8 +123,9 @@ def hs_ops(s, krawczyk=False):
 # case of the same kernel and scaled to a launch of the measured step by its own boxes per
 # launch: the traffic grows with the boxes a launch processes).
 TRAFFIC = {
-    ("n6", "hs_n6"): {"sources_sha256": "62891eeae8663b1de6d2d8d6266de4e64e29152cb3868fb6bbab36a76f7ec840",
-                      "bytes_per_launch": 485350, "default_options_only": True},
+    # profiles/k_hs_n6_dram.md: mean DRAM bytes of the stage per sweep of the n=6 solve
+    ("n6", "hs_n6"): {"sources_sha256": "c44aac276b43290460c0650e3d9a0e8ae810783df0d16dae8a9dc0db22b76c93",
+                      "bytes_per_launch": 479334, "default_options_only": True},
     # profiles/k_hs_n8_batched.md: 6.479 GB over 112,757,665 n = 8 boxes of all launches of a
     # solve with sweeps of 2^24 children (valid for that sweep size only: smaller sweeps
     # re-read more of their parents from DRAM)
