@@ -1,5 +1,6 @@
 """Host-side parts of bench.py that need no GPU: the clock sampler (against a stand-in
-nvidia-smi that prints rows in the query's CSV format) and the per-box work counts."""
+nvidia-smi that prints rows in the query's CSV format), the per-box work counts, and the
+guards on the DRAM traffic records."""
 
 import os
 import stat
@@ -59,3 +60,30 @@ def test_work_counts_of_the_n6_system():
     assert bench.hs_ops(s) == 2306
     assert bench.hs_ops(s, krawczyk=True) == 2342
     assert bench.eval_ops(s) == 304
+
+
+def test_traffic_records_apply_only_to_their_kernel_sources_and_sweep_size(monkeypatch):
+    """A DRAM traffic record is reported only for the kernel sources it was captured
+    with (code hash), for default options, and at the sweep size it was taken at; a per-box
+    record scales with the boxes a launch processes."""
+    rec = bench.TRAFFIC[("batched", "hs_n8")]
+    monkeypatch.setattr(bench, "hs_sources_sha", lambda read=None, files=bench.KERNEL_SOURCES: rec["sources_sha256"])
+    w = rec["wave_children"]
+    assert bench.traffic_of("batched", "hs_n8", True, 1000, w) == rec["bytes_per_hs_box"] * 1000
+    assert bench.traffic_of("batched", "hs_n8", True, 1000, w // 4) is None     # another sweep size
+    assert bench.traffic_of("batched", "hs_n8", False, 1000, w) is None         # non-default options
+    assert bench.traffic_of("batched", "hs_n8", True, None, w) is None          # boxes per launch unknown
+    assert bench.traffic_of("batched", "eval", True, 1000, w) is None           # no record
+    monkeypatch.setattr(bench, "hs_sources_sha", lambda read=None, files=bench.KERNEL_SOURCES: "0" * 64)
+    assert bench.traffic_of("batched", "hs_n8", True, 1000, w) is None          # kernel sources changed
+
+
+def test_code_hash_ignores_comments_and_whitespace():
+    a = "int f(int x) {  // a comment\n  return x + 1; /* block\n comment */ }\n"
+    b = "int f(int x) {\n\treturn x + 1; }"
+    c = "int f(int x) { return x + 2; }"
+    src = {"a": a, "b": b, "c": c}
+    ha = bench.hs_sources_sha(read=lambda f: src["a"], files=("x",))
+    hb = bench.hs_sources_sha(read=lambda f: src["b"], files=("x",))
+    hc = bench.hs_sources_sha(read=lambda f: src["c"], files=("x",))
+    assert ha == hb and ha != hc
