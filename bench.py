@@ -888,7 +888,7 @@ def run_served(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=3)   # one batched step is ~43 s on a GB300
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="batched")
     ap.add_argument("--impl", default="ivsolve")
