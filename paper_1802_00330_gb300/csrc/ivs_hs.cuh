@@ -7,9 +7,9 @@
 // works on box b, so each FP64 warp instruction carries BB different boxes; the warps
 // split what is independent within a box: the n^2 + n polynomials of J(X) and f(x), the
 // row updates of each Gauss-Jordan step, the columns of M = B J(X), and the
-// Gauss-Seidel products.  What is serial within a box (pivot choice, the fold of each
-// Gauss-Seidel row, extended division and intersection, accept / split) stays with the
-// box's owner thread (warp 0, lane b).
+// Gauss-Seidel products.  What is serial within a box stays with its owner thread (warp 0,
+// lane b): pivot choice, the intersections, accept / split; each Gauss-Seidel row's fold and
+// extended division run on two threads, lower ends on warp 0 and upper ends on warp 1.
 //
 // Why: GB300's FP64 pipe charges a whole warp instruction whatever the number of active
 // lanes, and a sweep has few boxes (often less than one warp per SM), so one thread per

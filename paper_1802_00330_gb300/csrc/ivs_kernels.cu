@@ -628,7 +628,8 @@ __device__ __forceinline__ void eval_parent(const SweepArgs &a, WaveCtl *ctl, co
 }
 
 // Children of the popped parents.  A wide sweep gives each warp a parent at a time from
-// a shared cursor (one lane per child); a narrow one (at most one parent per block)
+// a shared cursor (one lane per child, or two or four children per lane on the table
+// path when the fan-out fills that many rounds); a narrow one (at most one parent per block)
 // gives each block its parents and spreads a parent's table entries and children over
 // all of the block's threads, so the few parents of the first and last sweeps finish
 // sooner.  Both run the same per-child arithmetic.
